@@ -1,0 +1,253 @@
+/*
+ * CPU oracle for UTF-8 validation — TEST INFRASTRUCTURE ONLY.
+ *
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+ * load this library.  The product path (the CUDA kernels behind
+ * libutf8gpu.so) never calls it and shares no code, header or table with it.
+ *
+ * What it computes: the RFC 3629 well-formedness predicate that the paper
+ * states in Section 3 (Table 1: the valid code-point ranges and their byte
+ * forms; rules a-f: 5+ byte, too short, too long, overlong, too large,
+ * surrogate).  The `lookup` algorithm of Section 6 reaches exactly this
+ * boolean, so the oracle is that definition written out as a plain decode
+ * loop: read a lead byte, decide the sequence length from its header bits,
+ * check and accumulate the continuation bytes, then range-check the decoded
+ * code point.  It is branchy and slow on purpose.
+ *
+ * A second, independent validator, the finite-state machine of Section 5
+ * (its state-transition table), lives here as well.  It is not the oracle;
+ * the tests use it as one more pin on the oracle (exhaustive agreement on
+ * short strings).
+ *
+ * Build: gcc -O2 -shared -fPIC -o liboracle.so utf8_oracle.c -lpthread
+ * With -DORACLE_MUTANT=k one deliberate mistake is planted (tests only),
+ * to show that the pins catch it.
+ */
+#include <stddef.h>
+#include <stdint.h>
+#include <pthread.h>
+
+#ifndef ORACLE_MUTANT
+#define ORACLE_MUTANT 0
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* The oracle: decode and range-check (Section 3, Table 1, rules a-f).       */
+/* ------------------------------------------------------------------------ */
+int oracle_valid(const uint8_t* s, size_t n)
+{
+    size_t i = 0;
+    while (i < n) {
+        uint32_t lead = s[i];
+        uint32_t len, cp, min_cp;
+        if (lead < 0x80) {                 /* 1 byte: ASCII U+0000..U+007F */
+            i += 1;
+            continue;
+        } else if ((lead >> 5) == 0x6) {   /* 110xxxxx: 2 bytes, >= U+0080 */
+            len = 2; cp = lead & 0x1F; min_cp = 0x80;
+        } else if ((lead >> 4) == 0xE) {   /* 1110xxxx: 3 bytes, >= U+0800 */
+            len = 3; cp = lead & 0x0F; min_cp = 0x800;
+#if ORACLE_MUTANT == 1                      /* mutant: wrong overlong bound */
+            min_cp = 0x80;
+#endif
+        } else if ((lead >> 3) == 0x1E) {  /* 11110xxx: 4 bytes, >= U+10000 */
+            len = 4; cp = lead & 0x07; min_cp = 0x10000;
+#if ORACLE_MUTANT == 2                      /* mutant: 5-byte leads admitted */
+        } else if ((lead >> 2) == 0x3E) {
+            len = 4; cp = lead & 0x03; min_cp = 0x10000;
+#endif
+        } else {
+            /* rule c (a continuation byte 10xxxxxx cannot lead) or
+             * rule a (five or more header bits: 11111xxx) */
+            return 0;
+        }
+#if ORACLE_MUTANT == 3                      /* mutant: truncated tail ignored */
+        if (n - i < len) return 1;
+#else
+        if (n - i < len) return 0;         /* rule b: too short at the end */
+#endif
+        for (uint32_t k = 1; k < len; ++k) {
+            uint32_t c = s[i + k];
+#if ORACLE_MUTANT == 4                      /* mutant: any byte >= 0x80 continues */
+            if (c < 0x80) return 0;
+#else
+            if ((c >> 6) != 0x2) return 0; /* rule b: not a continuation */
+#endif
+            cp = (cp << 6) | (c & 0x3F);
+        }
+        if (cp < min_cp) return 0;         /* rule d: overlong */
+#if ORACLE_MUTANT == 5                      /* mutant: off-by-one upper bound */
+        if (cp > 0x110000) return 0;
+#else
+        if (cp > 0x10FFFF) return 0;       /* rule e: too large */
+#endif
+#if ORACLE_MUTANT != 6                      /* mutant 6: surrogates admitted */
+        if (cp >= 0xD800 && cp <= 0xDFFF) return 0;  /* rule f: surrogate */
+#endif
+        i += len;
+    }
+    return 1;                              /* the empty string is valid */
+}
+
+/* One flag per string: string k is s[offsets[k] .. offsets[k+1]). */
+static void batch_range(const uint8_t* data, const int64_t* offsets,
+                        int64_t lo, int64_t hi, uint8_t* out)
+{
+    for (int64_t k = lo; k < hi; ++k)
+        out[k] = (uint8_t)oracle_valid(data + offsets[k],
+                                       (size_t)(offsets[k + 1] - offsets[k]));
+}
+
+typedef struct {
+    const uint8_t* data; const int64_t* offsets; int64_t lo, hi; uint8_t* out;
+} batch_job;
+
+static void* batch_worker(void* arg)
+{
+    batch_job* j = (batch_job*)arg;
+    batch_range(j->data, j->offsets, j->lo, j->hi, j->out);
+    return NULL;
+}
+
+/* Validates `count` strings; `threads` > 1 splits the string list into equal
+ * contiguous slices, one POSIX thread each (strings are independent). */
+void oracle_valid_batch(const uint8_t* data, const int64_t* offsets,
+                        int64_t count, uint8_t* out, int threads)
+{
+    if (threads <= 1 || count < 2 * threads) {
+        batch_range(data, offsets, 0, count, out);
+        return;
+    }
+    if (threads > 256) threads = 256;
+    pthread_t tid[256];
+    batch_job job[256];
+    for (int t = 0; t < threads; ++t) {
+        job[t].data = data; job[t].offsets = offsets; job[t].out = out;
+        job[t].lo = count * t / threads;
+        job[t].hi = count * (t + 1) / threads;
+        pthread_create(&tid[t], NULL, batch_worker, &job[t]);
+    }
+    for (int t = 0; t < threads; ++t) pthread_join(tid[t], NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Independent pin: the finite-state validator of Section 5.                */
+/*                                                                          */
+/* Byte categories: the three continuation ranges (the reading taken is     */
+/* Low 80..8F, Mid 90..9F, High A0..BF, the one consistent with the         */
+/* transitions) and the nine first-byte rows of the transition table.       */
+/* ------------------------------------------------------------------------ */
+enum { C_LOW, C_MID, C_HIGH,                     /* continuation bytes */
+       F_ASCII, F_2, F_3, F_4, F_E0, F_ED, F_F0, F_F4, F_BAD, N_CAT };
+enum { S_VALID, S_1, S_2, S_3, S_E0, S_ED, S_F0, S_F4, S_ERROR, N_STATE };
+
+static int fsm_category(uint32_t b)
+{
+    if (b <= 0x7F) return F_ASCII;
+    if (b <= 0x8F) return C_LOW;
+    if (b <= 0x9F) return C_MID;
+    if (b <= 0xBF) return C_HIGH;
+    if (b <= 0xC1) return F_BAD;                 /* 110 00000..00001 */
+    if (b <= 0xDF) return F_2;                   /* 110 00010..11111 */
+    if (b == 0xE0) return F_E0;
+    if (b == 0xED) return F_ED;
+    if (b <= 0xEF) return F_3;                   /* E1..EC, EE..EF */
+    if (b == 0xF0) return F_F0;
+    if (b <= 0xF3) return F_4;                   /* F1..F3 */
+    if (b == 0xF4) return F_F4;
+    return F_BAD;                                /* F5..FF */
+}
+
+static int fsm_next(int state, int cat)
+{
+    int cont = (cat == C_LOW || cat == C_MID || cat == C_HIGH);
+    switch (state) {
+    case S_VALID:
+        switch (cat) {
+        case F_ASCII: return S_VALID;
+        case F_2: return S_1;
+        case F_3: return S_2;
+        case F_4: return S_3;
+        case F_E0: return S_E0;
+        case F_ED: return S_ED;
+        case F_F0: return S_F0;
+        case F_F4: return S_F4;
+        default: return S_ERROR;                 /* continuation or bad lead */
+        }
+    case S_1: return cont ? S_VALID : S_ERROR;
+    case S_2: return cont ? S_1 : S_ERROR;
+    case S_3: return cont ? S_2 : S_ERROR;
+    case S_E0: return cat == C_HIGH ? S_1 : S_ERROR;           /* 3-byte overlong */
+    case S_ED: return (cat == C_LOW || cat == C_MID) ? S_1 : S_ERROR; /* surrogate */
+    case S_F0: return (cat == C_MID || cat == C_HIGH) ? S_2 : S_ERROR; /* 4-byte overlong */
+    case S_F4: return cat == C_LOW ? S_2 : S_ERROR;            /* too large */
+    default: return S_ERROR;                                    /* sticky */
+    }
+}
+
+int oracle_fsm_valid(const uint8_t* s, size_t n)
+{
+    int state = S_VALID;
+    for (size_t i = 0; i < n; ++i) state = fsm_next(state, fsm_category(s[i]));
+    return state == S_VALID;     /* ending mid-character is an error */
+}
+
+/* ------------------------------------------------------------------------ */
+/* Enumeration helpers for the exhaustive pins (tests only).                */
+/* ------------------------------------------------------------------------ */
+
+/* Counts valid strings among all byte strings of length `len` (1..4) whose
+ * first byte is >= lead_min, using the decode oracle (which = 0) or the
+ * finite-state validator (which = 1). */
+int64_t oracle_count_valid(int len, int lead_min, int which)
+{
+    uint8_t s[4];
+    int64_t count = 0;
+    uint64_t total = 1;
+    for (int k = 1; k < len; ++k) total <<= 8;
+    for (uint32_t b0 = (uint32_t)lead_min; b0 < 256; ++b0) {
+        s[0] = (uint8_t)b0;
+        for (uint64_t r = 0; r < total; ++r) {
+            for (int k = 1; k < len; ++k) s[k] = (uint8_t)(r >> (8 * (k - 1)));
+            int v = which ? oracle_fsm_valid(s, (size_t)len) : oracle_valid(s, (size_t)len);
+            count += v;
+        }
+    }
+    return count;
+}
+
+/* Writes validity of every string of length `len` (1..3) into out[256^len],
+ * indexed by the string read as a little-endian integer. */
+void oracle_valid_all(int len, uint8_t* out, int which)
+{
+    uint8_t s[3];
+    uint64_t total = 1;
+    for (int k = 0; k < len; ++k) total <<= 8;
+    for (uint64_t r = 0; r < total; ++r) {
+        for (int k = 0; k < len; ++k) s[k] = (uint8_t)(r >> (8 * k));
+        out[r] = (uint8_t)(which ? oracle_fsm_valid(s, (size_t)len)
+                                 : oracle_valid(s, (size_t)len));
+    }
+}
+
+/* Agreement of the decode oracle and the finite-state validator over every
+ * string of byte classes of length 1..max_len, one representative byte per
+ * class taken from reps[0..nreps).  Returns the number of disagreements. */
+int64_t oracle_class_disagreements(const uint8_t* reps, int nreps, int max_len)
+{
+    uint8_t s[16];
+    int idx[16];
+    int64_t bad = 0;
+    if (max_len > 16) max_len = 16;
+    for (int len = 1; len <= max_len; ++len) {
+        for (int k = 0; k < len; ++k) idx[k] = 0;
+        for (;;) {
+            for (int k = 0; k < len; ++k) s[k] = reps[idx[k]];
+            if (oracle_valid(s, (size_t)len) != oracle_fsm_valid(s, (size_t)len)) ++bad;
+            int k = 0;
+            while (k < len && ++idx[k] == nreps) idx[k++] = 0;
+            if (k == len) break;
+        }
+    }
+    return bad;
+}
