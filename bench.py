@@ -1,0 +1,433 @@
+#!/usr/bin/env python
+"""Benchmark of the GPU `lookup` UTF-8 validator (one JSON line on rank 0).
+
+Workload (one step): the five 1 GiB seeded content variants (pure ASCII,
+Latin-like, CJK-like, emoji-heavy, uniform 1-4 byte mix) plus a copy of each
+whose last 3 bytes hold a truncated character: ten 1 GiB buffers, each
+validated by one utf8_validate_async call (a 1-byte memset and one
+validate_kernel launch) on one stream.  Inputs are resident in HBM before the
+timed region; each buffer is larger than the 129 MB L2, so nothing is served
+from L2 across iterations.
+
+Metric: validated GB/s (1e9 input bytes per second), whole job.  Beside it:
+% of the measured HBM copy peak, the kernel roofline, the end-to-end rate of
+the host-memory entry point (pinned host buffers copied in every step), the
+oracle on the host cores (a bounded sample), and two secondary measurements:
+the 1M-string batch against launching one validation per string, and the
+serving loop's latency percentiles.
+
+--impl reference times the CPU oracle (the only reference that exists for
+this method) on the same workload, a bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+GIB = 1 << 30
+NOMINAL_HBM_GBS = 8000.0
+FALLBACK_HBM_GBS = 6800.0
+METRIC = "validated GB/s"
+WORKLOAD = ("single 1 GiB buffers: 5 seeded content variants (ascii, latin, cjk, emoji, "
+            "uniform 1-4 byte) + a truncated-tail copy of each = 10 GiB per step")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--buffer-bytes", type=int, default=GIB)
+    ap.add_argument("--no-extras", action="store_true", help="skip batch/serving extras")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="CPU budget of the oracle baseline sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def char_start(buf: np.ndarray, p: int) -> int:
+    """Backs p up to a byte that is not a continuation (at most 3 bytes)."""
+    for _ in range(3):
+        if p <= 0 or (int(buf[p]) & 0xC0) != 0x80:
+            break
+        p -= 1
+    return p
+
+
+def make_workload(n: int, rank: int):
+    """Host arrays of the ten buffers (five clean variants, five tail-error)."""
+    import synth
+    bufs, names = [], []
+    for i, name in enumerate(synth.VARIANTS_1GIB):
+        seed = synth.SEED_BASE + 1000 + i + 100 * rank
+        clean = synth.fill_variant(n, name, seed)
+        bad = clean.copy()
+        bad[-3:] = np.frombuffer(synth.tail_error_bytes(seed), np.uint8)
+        bufs += [clean, bad]
+        names += [name, name + "+tail"]
+    return bufs, names
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[4:8]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (same hash); None otherwise."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_hash") != source_hash():
+        return None
+    return rec
+
+
+def source_hash() -> str:
+    csrc = os.path.join(ROOT, "paper_2010_03090_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def oracle_baseline(bufs, names, seconds: float) -> dict:
+    """The oracle, single-threaded, on the tail of every buffer (from a
+    character start, so each sample's validity equals its buffer's)."""
+    import oracle
+    probe = [oracle.valid(b[: 8 << 20]) for b in bufs[:1]]  # warm the library
+    del probe
+    t = time.perf_counter()
+    for b in bufs:
+        oracle.valid(b[-(4 << 20):])
+    rate = 10 * (4 << 20) / max(time.perf_counter() - t, 1e-9)
+    per = int(min(max(rate * seconds / len(bufs), 1 << 20), bufs[0].size))
+    samples = [b[char_start(b, b.size - per):] for b in bufs]
+    t = time.perf_counter()
+    got = [oracle.valid(s) for s in samples]
+    dt = time.perf_counter() - t
+    total = sum(s.size for s in samples)
+    return {"value": round(total / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"last {per >> 20} MiB (from a character start) of each of the "
+                      f"{len(bufs)} buffers, {total / 1e9:.2f} GB, {dt:.1f} s, one thread",
+            "flags": dict(zip(names, got))}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    n = args.buffer_bytes
+    bufs, names = make_workload(n, 0)
+    # size each step's sample so that warmup + steps take about two minutes
+    total_budget = 120.0
+    t = time.perf_counter()
+    for b in bufs:
+        oracle.valid(b[-(2 << 20):])
+    rate = 10 * (2 << 20) / max(time.perf_counter() - t, 1e-9)
+    per_step = max(rate * total_budget / max(args.steps + args.warmup, 1), 10 * 4096)
+    per = int(min(per_step / len(bufs), n))
+    samples = [b[char_start(b, b.size - per):] for b in bufs]
+    step_bytes = sum(s.size for s in samples)
+    for _ in range(args.warmup):
+        for s in samples:
+            oracle.valid(s)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        flags = [oracle.valid(s) for s in samples]
+    dt = time.perf_counter() - t
+    value = step_bytes * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / max(args.steps, 1) * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_per_step_bytes": step_bytes,
+                   "l2": "host CPU; no GPU involved"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: last {per} bytes (from a character start) of "
+                                   f"each of the 10 buffers, one thread"},
+        "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "flags": dict(zip(names, flags)),
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import torch
+    import paper_2010_03090_gb300 as u
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    n = args.buffer_bytes
+    host, names = make_workload(n, rank)
+    dev = [torch.from_numpy(b).cuda() for b in host]
+    res = torch.empty(len(dev), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    bytes_per_step = sum(b.size for b in host)
+    u.lib()
+
+    def step(events=None, k=0):
+        for i, t in enumerate(dev):
+            if events is not None:
+                events[k][i][0].record(stream)
+            u.utf8_validate_async(t, res[i:i + 1], stream=stream)
+            if events is not None:
+                events[k][i][1].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            step()
+    stream.synchronize()
+    flags = res.cpu().numpy().tolist()
+
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in dev] for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    with torch.cuda.stream(stream):
+        start.record(stream)
+        for k in range(args.steps):
+            step(ev, k)
+        stop.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    elapsed_ms = start.elapsed_time(stop)
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    per_buf_ms = np.array([[a.elapsed_time(b) for a, b in row] for row in ev])
+    value = world * bytes_per_step * args.steps / (elapsed_ms / 1e3) / 1e9
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    peaks = measured_peaks()
+    peak = float(peaks.get("hbm_gbs") or FALLBACK_HBM_GBS)
+    kernel_time_s = per_buf_ms.sum() / 1e3
+    achieved = bytes_per_step * args.steps / kernel_time_s / 1e9
+    traffic = kernel_traffic("validate_kernel")
+    per_variant = {nm: round(host[i].size / (per_buf_ms[:, i].mean() / 1e3) / 1e9, 1)
+                   for i, nm in enumerate(names)}
+    cfg = json.loads(u.utf8_config_json())
+
+    # end to end: host buffers through the public host-memory entry point
+    e2e_steps = max(2, min(args.steps, 5))
+    pinned = []
+    for b in host:
+        p = torch.empty(b.size, dtype=torch.uint8, pin_memory=True)
+        p.numpy()[:] = b
+        pinned.append(p)
+    u.utf8_validate_host(pinned[0][: 1 << 20], stream=stream)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_flags = [u.utf8_validate_host(p, stream=stream) for p in pinned]
+    e2e_dt = time.perf_counter() - t
+    e2e_value = bytes_per_step * e2e_steps / e2e_dt / 1e9
+    del pinned
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded generators; the paper's files are not available)",
+        "config": {"workload": WORKLOAD, "bytes_per_step": bytes_per_step,
+                   "l2": "inputs larger than L2 (each buffer 1 GiB > 129 MB L2)",
+                   "launch": cfg},
+        "pct_of_hbm_peak": {"measured": round(100 * value / world / peak, 1),
+                            "nominal_8000": round(100 * value / world / NOMINAL_HBM_GBS, 1)},
+        "roofline": {"bound": "hbm", "kernel": "validate_kernel",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4),
+                     "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback",
+                     "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                     "algorithmic_bytes_per_launch": n},
+        "per_variant_gbs": per_variant,
+        "flags": dict(zip(names, flags)),
+        "e2e": {"value": round(e2e_value, 1), "unit": "GB/s",
+                "h2d_bytes_per_step": bytes_per_step, "d2h_bytes_per_step": len(host),
+                "steps": e2e_steps, "api": "utf8_validate_host (pinned host buffers)",
+                "flags_ok": [bool(f) for f in e2e_flags] == [bool(f) for f in flags]},
+        "gpu_launches": len(dev) * args.steps,
+        "clocks": clock_info,
+    }
+    if world == 1:
+        line["cpu_baseline"] = oracle_baseline(host, names, args.cpu_seconds)
+    if not args.no_extras and world == 1:
+        del dev
+        torch.cuda.empty_cache()
+        line["batched_1m"] = bench_batch(u, torch, stream, peak)
+        try:
+            from paper_2010_03090_gb300 import serve
+            line["serving"] = serve.bench_serving(stream=stream)
+        except ImportError:
+            pass
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def bench_batch(u, torch, stream, peak: float) -> dict:
+    """1M strings in one batch vs one launch per string (a sample)."""
+    import synth
+    data, offsets, _ = synth.workload_batch_1m()
+    d = torch.from_numpy(data).cuda()
+    o = torch.from_numpy(offsets).cuda()
+    out = torch.empty(offsets.size - 1, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            u.utf8_validate_batch(d, o, out, stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 30
+        a.record(stream)
+        for _ in range(reps):
+            u.utf8_validate_batch(d, o, out, stream=stream)
+        b.record(stream)
+    stream.synchronize()
+    ms = a.elapsed_time(b) / reps
+    batch_gbs = data.size / (ms / 1e3) / 1e9
+    moved = data.size + offsets.nbytes + (offsets.size - 1)
+    # per-string launches on a sample of consecutive strings
+    sample = 20000
+    one = torch.empty(1, dtype=torch.uint8, device="cuda")
+    views = [d[offsets[i]:offsets[i + 1]] for i in range(sample)]
+    with torch.cuda.stream(stream):
+        for v in views[:100]:
+            u.utf8_validate_async(v, one, stream=stream)
+        stream.synchronize()
+        t = time.perf_counter()
+        for v in views:
+            u.utf8_validate_async(v, one, stream=stream)
+        stream.synchronize()
+        per_ms = (time.perf_counter() - t) * 1e3
+    per_gbs = int(offsets[sample] - offsets[0]) / (per_ms / 1e3) / 1e9
+    return {"strings": int(offsets.size - 1), "bytes": int(data.size),
+            "ms": round(ms, 4), "gbs": round(batch_gbs, 1),
+            "pct_of_hbm_peak": round(100 * moved / (ms / 1e3) / 1e9 / peak, 1),
+            "per_string_launch_gbs": round(per_gbs, 3),
+            "per_string_launch_sample": sample,
+            "speedup_vs_per_string": round(batch_gbs / per_gbs, 1)}
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    import synth
+    synth.build()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

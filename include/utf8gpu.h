@@ -1,0 +1,140 @@
+/*
+ * utf8gpu — UTF-8 validation on one GPU with the `lookup` algorithm of
+ * J. Keiser and D. Lemire, "Validating UTF-8 In Less Than One Instruction Per
+ * Byte" (Software: Practice and Experience, 2021; arXiv 2010.03090).
+ *
+ * The problem (Section 3): a byte sequence is valid UTF-8 iff it splits into
+ * characters of Table 1 -- one ASCII byte 00..7F, or a lead byte with 2..4
+ * header bits followed by 1..3 continuation bytes 10xxxxxx -- where the
+ * decoded code point is not overlong (rule d), not above U+10FFFF (rule e)
+ * and not a surrogate U+D800..U+DFFF (rule f).  The empty sequence is valid.
+ * Every entry point computes exactly this predicate, with the three nibble
+ * tables, the 3-4 byte check, the end-of-stream check and the ASCII early-out
+ * of Section 6, in hand-written CUDA kernels.  There is no CPU fallback: a
+ * machine without a usable GPU gets UTF8_ERR_CUDA.
+ *
+ * Conventions for every entry point
+ *   - Pointers named `data`, `offsets`, `out_*` are DEVICE pointers (memory
+ *     from cudaMalloc, or managed memory), unless the name says `host`.  The
+ *     caller owns all buffers; the library keeps no reference after the work
+ *     it queued has run.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     queued on it; entry points documented as asynchronous return before the
+ *     GPU has finished and the caller must keep the buffers alive until the
+ *     stream passes that point.
+ *   - Status: 0 (UTF8_OK) or a UTF8_ERR_* code.  The status of the calling
+ *     thread's last call is also kept for utf8_last_error(), which is the only
+ *     way to see it for utf8_validate(), whose result is a bool.
+ *   - The library allocates small per-device work areas on a device's first
+ *     call (a ring of result bytes and its pinned host mirror; the staging
+ *     buffer of utf8_validate_host on its first use); make that first call
+ *     before capturing any stream into a CUDA graph.  It never frees caller
+ *     memory.  Entry points are thread safe.
+ */
+#ifndef UTF8GPU_H
+#define UTF8GPU_H
+
+#include <stdbool.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum utf8_status {
+    UTF8_OK = 0,
+    UTF8_ERR_INVALID_ARG = 1, /* null pointer with len > 0, count < 0, host memory
+                                 passed where device memory is required, ... */
+    UTF8_ERR_CUDA = 2,        /* a CUDA call failed (no device, launch error, ...) */
+    UTF8_ERR_TIMEOUT = 3,     /* a device-side wait ran past its deadline */
+    UTF8_ERR_BUDGET = 4,      /* a request would exceed a memory budget */
+    UTF8_ERR_NOMEM = 5        /* a library work area could not be allocated */
+};
+
+/*
+ * Validates one buffer: data[0 .. len).  Returns true iff it is valid UTF-8.
+ * Section 3 defines the predicate; Section 6 (Fig. 1, Table 7, Sections
+ * 6.2-6.4) the algorithm.  len == 0 returns true without touching the GPU.
+ * Synchronises `stream` before returning.  On any error returns false and
+ * sets utf8_last_error() (UTF8_ERR_INVALID_ARG for data == NULL with len > 0
+ * or for a pointer that is not device memory).
+ */
+bool utf8_validate(const uint8_t* data, size_t len, cudaStream_t stream);
+
+/*
+ * Asynchronous form of utf8_validate: queues the work on `stream` and writes
+ * the result to the device byte *out_valid (1 = valid, 0 = invalid) when the
+ * stream reaches it.  Makes no synchronisation and no allocation, so it can be
+ * captured in a CUDA graph.  Returns a status.
+ */
+int utf8_validate_async(const uint8_t* data, size_t len, uint8_t* out_valid,
+                        cudaStream_t stream);
+
+/*
+ * Validates `count` strings in one launch sequence.  String i is
+ * data[offsets[i] .. offsets[i+1]) (int64 device array of count + 1
+ * non-decreasing entries, offsets[0] >= 0); each string is checked on its own
+ * (three virtual zero bytes before and after it, Section 6.3), never seeing
+ * its neighbours' bytes.  out_valid: device uint8[count], 1 = valid, 0 =
+ * invalid.  data must be non-null (and device memory) even when every string
+ * is empty.  Asynchronous on `stream`.  count == 0 is a no-op.  Offsets are not
+ * checked on the device; decreasing offsets give unspecified flags (never an
+ * out-of-range access beyond [data + offsets[0], data + offsets[count]) is
+ * made by a well-formed call).  Returns a status.
+ */
+int utf8_validate_batch(const uint8_t* data, const int64_t* offsets, int64_t count,
+                        uint8_t* out_valid, cudaStream_t stream);
+
+/*
+ * Validates a buffer in HOST memory: copies it to the GPU through a
+ * library-owned staging ring (pinned or pageable source; chunks of the copy
+ * overlap with validation of earlier chunks, the 3 bytes before each chunk
+ * carried across) and returns true iff it is valid UTF-8.  Synchronous.  On
+ * error returns false and sets utf8_last_error().
+ */
+bool utf8_validate_host(const uint8_t* host_data, size_t len, cudaStream_t stream);
+
+/*
+ * Debug view of the classification (Fig. 1 and Section 6.2) of one buffer:
+ * for each position i in 0 .. len+2 (the buffer followed by its three zero
+ * padding bytes) writes special_cases[i] = byte_1_high & byte_1_low &
+ * byte_2_high of (data[i-1], data[i]) and must23[i] = 0x80 where two
+ * continuations are expected (data[i-2] >= 0xE0 or data[i-3] >= 0xF0), with
+ * zeros before the buffer.  out_special, out_must23: device uint8[len + 3].
+ * Uses the same device code as the validators.  Asynchronous.
+ */
+int utf8_classify_debug(const uint8_t* data, size_t len, uint8_t* out_special,
+                        uint8_t* out_must23, cudaStream_t stream);
+
+/* Status of the calling thread's last utf8_* call. */
+int utf8_last_error(void);
+
+/* Static, human-readable text for a status code. */
+const char* utf8_error_string(int code);
+
+/*
+ * Autotuning of the launch configuration (tile rows per warp and resident
+ * CTAs per SM, for the single-buffer and the batch kernel) on synthetic data
+ * generated on the current device.
+ * flags: 0 = tune only what has no cached entry, 1 = retune everything.
+ * The cache is keyed by GPU name and SM count; it can be saved to and loaded
+ * from a JSON file.  Return a status.
+ */
+int utf8_autotune(int flags);
+int utf8_tune_cache_load(const char* path);
+int utf8_tune_cache_save(const char* path);
+
+/*
+ * Writes the launch configuration in use on the current device as a short
+ * JSON object into buf (at most cap bytes, NUL terminated).  Returns the
+ * length it needed, or -1.
+ */
+int utf8_config_json(char* buf, size_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UTF8GPU_H */

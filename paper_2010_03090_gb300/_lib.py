@@ -1,0 +1,197 @@
+"""ctypes binding of libutf8gpu.so (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+EXPORTS = (
+    "utf8_validate", "utf8_validate_async", "utf8_validate_batch", "utf8_validate_host",
+    "utf8_classify_debug", "utf8_last_error", "utf8_error_string", "utf8_autotune",
+    "utf8_tune_cache_load", "utf8_tune_cache_save", "utf8_config_json",
+)
+
+
+class Utf8Error(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = lib().utf8_error_string(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} (status {code})" if what else f"{msg} (status {code})")
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Loads the library (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            vp, sz, i64, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64, ctypes.c_int
+            L.utf8_validate.argtypes = [vp, sz, vp]
+            L.utf8_validate.restype = ctypes.c_bool
+            L.utf8_validate_async.argtypes = [vp, sz, vp, vp]
+            L.utf8_validate_async.restype = i32
+            L.utf8_validate_batch.argtypes = [vp, vp, i64, vp, vp]
+            L.utf8_validate_batch.restype = i32
+            L.utf8_validate_host.argtypes = [vp, sz, vp]
+            L.utf8_validate_host.restype = ctypes.c_bool
+            L.utf8_classify_debug.argtypes = [vp, sz, vp, vp, vp]
+            L.utf8_classify_debug.restype = i32
+            L.utf8_last_error.argtypes = []
+            L.utf8_last_error.restype = i32
+            L.utf8_error_string.argtypes = [i32]
+            L.utf8_error_string.restype = ctypes.c_char_p
+            L.utf8_autotune.argtypes = [i32]
+            L.utf8_autotune.restype = i32
+            L.utf8_tune_cache_load.argtypes = [ctypes.c_char_p]
+            L.utf8_tune_cache_load.restype = i32
+            L.utf8_tune_cache_save.argtypes = [ctypes.c_char_p]
+            L.utf8_tune_cache_save.restype = i32
+            L.utf8_config_json.argtypes = [ctypes.c_char_p, sz]
+            L.utf8_config_json.restype = i32
+            _lib = L
+    return _lib
+
+
+# --------------------------------------------------------------------------
+# marshalling helpers
+# --------------------------------------------------------------------------
+def _stream(stream):
+    if stream is None:
+        import torch
+        if not torch.cuda.is_available():
+            return None  # the library reports UTF8_ERR_CUDA itself
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _dev(t, dtype_name: str, what: str):
+    """(pointer, element count) of a contiguous CUDA tensor, or raw (ptr, n)."""
+    if isinstance(t, tuple):
+        return int(t[0]), int(t[1])
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what}: expected a torch tensor")
+    if not t.is_cuda:
+        raise Utf8Error(1, f"{what} must be CUDA device memory")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise TypeError(f"{what}: expected {dtype_name}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: tensor must be contiguous")
+    return t.data_ptr(), t.numel()
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise Utf8Error(status, what)
+
+
+# --------------------------------------------------------------------------
+# the C-ABI, same names
+# --------------------------------------------------------------------------
+def utf8_validate(data, stream=None) -> bool:
+    """True iff the uint8 CUDA tensor holds valid UTF-8 (synchronises the stream)."""
+    p, n = _dev(data, "uint8", "data")
+    ok = lib().utf8_validate(p or None, n, _stream(stream))
+    _check(lib().utf8_last_error(), "utf8_validate")
+    return bool(ok)
+
+
+def utf8_validate_async(data, out_valid=None, stream=None):
+    """Queues validation; returns a 1-element uint8 CUDA tensor (1 = valid)."""
+    import torch
+    p, n = _dev(data, "uint8", "data")
+    if out_valid is None:
+        out_valid = torch.empty(1, dtype=torch.uint8, device=data.device)
+    q, _ = _dev(out_valid, "uint8", "out_valid")
+    _check(lib().utf8_validate_async(p or None, n, q, _stream(stream)), "utf8_validate_async")
+    return out_valid
+
+
+def utf8_validate_batch(data, offsets, out_valid=None, stream=None):
+    """One uint8 flag per string data[offsets[i]:offsets[i+1]] (asynchronous)."""
+    import torch
+    if isinstance(data, torch.Tensor) and data.numel() == 0:
+        data = torch.zeros(16, dtype=torch.uint8, device=offsets.device)  # any device byte
+    p, _ = _dev(data, "uint8", "data")
+    q, m = _dev(offsets, "int64", "offsets")
+    count = m - 1
+    if count < 0:
+        raise ValueError("offsets needs at least one entry")
+    if out_valid is None:
+        out_valid = torch.empty(max(count, 0), dtype=torch.uint8, device=offsets.device)
+    r, k = _dev(out_valid, "uint8", "out_valid")
+    if k < count:
+        raise ValueError("out_valid is too small")
+    _check(lib().utf8_validate_batch(p or None, q, count, r, _stream(stream)),
+           "utf8_validate_batch")
+    return out_valid
+
+
+def utf8_validate_host(host, stream=None) -> bool:
+    """True iff the host buffer (numpy uint8 array, bytes or a CPU tensor,
+    pinned or not) is valid UTF-8; the library stages it through the GPU."""
+    keep = host
+    if isinstance(host, (bytes, bytearray)):
+        keep = (ctypes.c_uint8 * len(host)).from_buffer_copy(host)
+        p, n = ctypes.addressof(keep), len(host)
+    elif hasattr(host, "ctypes"):  # numpy
+        p, n = host.ctypes.data, host.nbytes
+    else:  # torch CPU tensor
+        if host.is_cuda:
+            raise Utf8Error(1, "utf8_validate_host needs host memory")
+        p, n = host.data_ptr(), host.numel() * host.element_size()
+    ok = lib().utf8_validate_host(p or None, n, _stream(stream))
+    del keep
+    _check(lib().utf8_last_error(), "utf8_validate_host")
+    return bool(ok)
+
+
+def utf8_classify_debug(data, stream=None):
+    """Per-position special_cases and must_be_2_3 bytes (len + 3 each)."""
+    import torch
+    p, n = _dev(data, "uint8", "data")
+    sc = torch.empty(n + 3, dtype=torch.uint8, device=data.device)
+    m = torch.empty(n + 3, dtype=torch.uint8, device=data.device)
+    _check(lib().utf8_classify_debug(p or None, n, sc.data_ptr(), m.data_ptr(), _stream(stream)),
+           "utf8_classify_debug")
+    return sc, m
+
+
+def utf8_last_error() -> int:
+    return lib().utf8_last_error()
+
+
+def utf8_error_string(code: int) -> str:
+    return lib().utf8_error_string(code).decode()
+
+
+def utf8_autotune(flags: int = 0) -> None:
+    _check(lib().utf8_autotune(flags), "utf8_autotune")
+
+
+def utf8_tune_cache_load(path: str) -> None:
+    _check(lib().utf8_tune_cache_load(os.fsencode(path)), "utf8_tune_cache_load")
+
+
+def utf8_tune_cache_save(path: str) -> None:
+    _check(lib().utf8_tune_cache_save(os.fsencode(path)), "utf8_tune_cache_save")
+
+
+def utf8_config_json() -> str:
+    buf = ctypes.create_string_buffer(512)
+    n = lib().utf8_config_json(buf, 512)
+    if n < 0:
+        raise Utf8Error(lib().utf8_last_error(), "utf8_config_json")
+    return buf.value.decode()

@@ -1,0 +1,308 @@
+// The C-ABI of libutf8gpu.so (declared in include/utf8gpu.h).
+//
+// Host-side runtime: per-device state (SM count, launch configuration, a ring
+// of result bytes with a pinned host mirror, the staging buffer and copy
+// stream of the host-memory path), argument checks and status codes.  All
+// validation work runs in the kernels of validate.cu and batch.cu; there is
+// no CPU path.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+
+#include "internal.h"
+#include "tune.h"
+#include "utf8gpu.h"
+
+namespace utf8gpu {
+
+namespace {
+
+thread_local int tl_status = UTF8_OK;
+
+inline int set_status(int s) {
+  tl_status = s;
+  return s;
+}
+
+constexpr int kMaxDevices = 64;
+constexpr uint32_t kResultSlots = 4096;
+constexpr uint64_t kStageChunk = 64ull << 20;   // bytes per pipelined host copy
+constexpr uint64_t kStageWindow = 4ull << 30;   // largest staging buffer
+constexpr int kStageEvents = 64;
+
+// UTF8GPU_STAGE_CHUNK / UTF8GPU_STAGE_WINDOW override the two sizes (bytes),
+// rounded to whole tiles.
+uint64_t env_size(const char* name, uint64_t fallback, uint64_t tile) {
+  const char* v = getenv(name);
+  uint64_t x = (v && *v) ? strtoull(v, nullptr, 10) : fallback;
+  x = (x / tile) * tile;
+  return x ? x : tile;
+}
+
+struct DeviceState {
+  std::once_flag once;
+  int init_error = cudaSuccess;
+  int sm_count = 0;
+  LaunchCfg cfg;
+  uint8_t* d_results = nullptr;  // kResultSlots result bytes
+  uint8_t* h_results = nullptr;  // pinned mirror
+  std::atomic<uint32_t> next_slot{0};
+  // host-memory path
+  std::mutex stage_mu;
+  uint8_t* d_stage = nullptr;
+  uint64_t stage_cap = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copied[kStageEvents] = {};
+  cudaEvent_t consumed = nullptr;
+};
+
+DeviceState g_dev[kMaxDevices];
+
+void init_device(DeviceState& d, int dev) {
+  cudaDeviceProp prop;
+  cudaError_t e = cudaGetDeviceProperties(&prop, dev);
+  if (e == cudaSuccess) {
+    d.sm_count = prop.multiProcessorCount;
+    d.cfg = tuned_config(prop.name, prop.multiProcessorCount);
+    clamp_to_occupancy(d.cfg);
+    e = cudaMalloc(&d.d_results, kResultSlots);
+  }
+  if (e == cudaSuccess) e = cudaHostAlloc(&d.h_results, kResultSlots, cudaHostAllocDefault);
+  d.init_error = e;
+}
+
+// State of the current device, or nullptr (status set) when CUDA fails.
+DeviceState* device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    set_status(UTF8_ERR_CUDA);
+    return nullptr;
+  }
+  DeviceState& d = g_dev[dev];
+  std::call_once(d.once, init_device, std::ref(d), dev);
+  if (d.init_error != cudaSuccess) {
+    set_status(UTF8_ERR_CUDA);
+    return nullptr;
+  }
+  return &d;
+}
+
+bool is_device_memory(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int cuda_status(cudaError_t e) { return set_status(e == cudaSuccess ? UTF8_OK : UTF8_ERR_CUDA); }
+
+}  // namespace
+
+LaunchCfg current_config() {
+  DeviceState* d = device();
+  return d ? d->cfg : LaunchCfg();
+}
+
+void set_current_config(const LaunchCfg& cfg) {
+  DeviceState* d = device();
+  if (d) {
+    d->cfg = cfg;
+    clamp_to_occupancy(d->cfg);
+  }
+}
+
+int current_sm_count() {
+  DeviceState* d = device();
+  return d ? d->sm_count : 0;
+}
+
+}  // namespace utf8gpu
+
+using namespace utf8gpu;
+
+extern "C" {
+
+bool utf8_validate(const uint8_t* data, size_t len, cudaStream_t stream) {
+  if (len == 0) return set_status(UTF8_OK), true;
+  if (data == nullptr) return set_status(UTF8_ERR_INVALID_ARG), false;
+  DeviceState* d = device();
+  if (!d) return false;
+  if (!is_device_memory(data)) return set_status(UTF8_ERR_INVALID_ARG), false;
+  const uint32_t slot = d->next_slot.fetch_add(1) % kResultSlots;
+  cudaError_t e = launch_validate(data, len, d->d_results + slot, d->cfg, d->sm_count, stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d->h_results + slot, d->d_results + slot, 1, cudaMemcpyDeviceToHost,
+                        stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_status(e), false;
+  set_status(UTF8_OK);
+  return d->h_results[slot] == 1;
+}
+
+int utf8_validate_async(const uint8_t* data, size_t len, uint8_t* out_valid,
+                        cudaStream_t stream) {
+  if (out_valid == nullptr || (data == nullptr && len > 0))
+    return set_status(UTF8_ERR_INVALID_ARG);
+  DeviceState* d = device();
+  if (!d) return UTF8_ERR_CUDA;
+  if (!is_device_memory(out_valid) || (len > 0 && !is_device_memory(data)))
+    return set_status(UTF8_ERR_INVALID_ARG);
+  if (len == 0) return cuda_status(cudaMemsetAsync(out_valid, 1, 1, stream));
+  return cuda_status(launch_validate(data, len, out_valid, d->cfg, d->sm_count, stream));
+}
+
+int utf8_validate_batch(const uint8_t* data, const int64_t* offsets, int64_t count,
+                        uint8_t* out_valid, cudaStream_t stream) {
+  if (count < 0) return set_status(UTF8_ERR_INVALID_ARG);
+  if (count == 0) return set_status(UTF8_OK);
+  if (data == nullptr || offsets == nullptr || out_valid == nullptr)
+    return set_status(UTF8_ERR_INVALID_ARG);
+  DeviceState* d = device();
+  if (!d) return UTF8_ERR_CUDA;
+  if (!is_device_memory(data) || !is_device_memory(offsets) || !is_device_memory(out_valid))
+    return set_status(UTF8_ERR_INVALID_ARG);
+  return cuda_status(launch_batch(data, offsets, count, out_valid, d->cfg, d->sm_count, stream));
+}
+
+bool utf8_validate_host(const uint8_t* host_data, size_t len, cudaStream_t stream) {
+  if (len == 0) return set_status(UTF8_OK), true;
+  if (host_data == nullptr) return set_status(UTF8_ERR_INVALID_ARG), false;
+  DeviceState* d = device();
+  if (!d) return false;
+  std::lock_guard<std::mutex> lock(d->stage_mu);
+  cudaError_t e = cudaSuccess;
+  const uint64_t tb = tile_bytes(d->cfg);
+  const uint64_t chunk = env_size("UTF8GPU_STAGE_CHUNK", kStageChunk, tb);
+  const uint64_t max_window = env_size("UTF8GPU_STAGE_WINDOW", kStageWindow, chunk);
+  // staging buffer: one halo tile + a window of whole chunks
+  const uint64_t window = len < max_window ? ((len + tb - 1) / tb) * tb : max_window;
+  const uint64_t need = tb + window;
+  if (d->stage_cap < need) {
+    if (d->d_stage) cudaFree(d->d_stage);
+    d->d_stage = nullptr;
+    d->stage_cap = 0;
+    e = cudaMalloc(&d->d_stage, need);
+    if (e != cudaSuccess) return cudaGetLastError(), set_status(UTF8_ERR_NOMEM), false;
+    d->stage_cap = need;
+  }
+  if (!d->copy_stream) {
+    e = cudaStreamCreateWithFlags(&d->copy_stream, cudaStreamNonBlocking);
+    for (int i = 0; e == cudaSuccess && i < kStageEvents; ++i)
+      e = cudaEventCreateWithFlags(&d->copied[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d->consumed, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_status(e), false;
+  }
+  const uint32_t slot = d->next_slot.fetch_add(1) % kResultSlots;
+  uint8_t* result = d->d_results + slot;
+  e = cudaMemsetAsync(result, 1, 1, stream);
+  // Window k holds host bytes [k*window, ...) at d_stage + tb, preceded by the
+  // tile of bytes before it (the halo) for k >= 1.
+  uint64_t chunk_id = 0;
+  for (uint64_t w0 = 0; e == cudaSuccess && w0 < len; w0 += window) {
+    const uint64_t wlen = len - w0 < window ? len - w0 : window;
+    const bool last_window = w0 + wlen == len;
+    const uint8_t* span_data = w0 == 0 ? d->d_stage + tb : d->d_stage;
+    const uint64_t span_n = w0 == 0 ? wlen : tb + wlen;
+    const uint64_t first_tile = w0 == 0 ? 0 : 1;
+    if (w0 > 0) {  // the previous window's kernels must be done with the buffer
+      e = cudaEventRecord(d->consumed, stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(d->copy_stream, d->consumed, 0);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d->d_stage, host_data + w0 - tb, tb, cudaMemcpyHostToDevice,
+                            d->copy_stream);
+    }
+    for (uint64_t c0 = 0; e == cudaSuccess && c0 < wlen; c0 += chunk) {
+      const uint64_t clen = wlen - c0 < chunk ? wlen - c0 : chunk;
+      const bool last_chunk = last_window && c0 + clen == wlen;
+      e = cudaMemcpyAsync(d->d_stage + tb + c0, host_data + w0 + c0, clen,
+                          cudaMemcpyHostToDevice, d->copy_stream);
+      cudaEvent_t ev = d->copied[chunk_id++ % kStageEvents];
+      if (e == cudaSuccess) e = cudaEventRecord(ev, d->copy_stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev, 0);
+      // tiles of the span that end inside the copied bytes (all remaining ones,
+      // padding included, after the last chunk)
+      const uint64_t done = (w0 == 0 ? 0 : tb) + c0 + clen;
+      const uint64_t t_begin = first_tile + (c0 / tb);
+      const uint64_t t_end = last_chunk ? ~uint64_t(0) : done / tb;
+      if (e == cudaSuccess)
+        e = launch_validate_tiles(span_data, span_n, t_begin, t_end, result, d->cfg, d->sm_count,
+                                  stream);
+    }
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d->h_results + slot, result, 1, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_status(e), false;
+  set_status(UTF8_OK);
+  return d->h_results[slot] == 1;
+}
+
+int utf8_classify_debug(const uint8_t* data, size_t len, uint8_t* out_special,
+                        uint8_t* out_must23, cudaStream_t stream) {
+  if (out_special == nullptr || out_must23 == nullptr || (data == nullptr && len > 0))
+    return set_status(UTF8_ERR_INVALID_ARG);
+  DeviceState* d = device();
+  if (!d) return UTF8_ERR_CUDA;
+  if (!is_device_memory(out_special) || !is_device_memory(out_must23) ||
+      (len > 0 && !is_device_memory(data)))
+    return set_status(UTF8_ERR_INVALID_ARG);
+  return cuda_status(launch_classify_debug(data, len, out_special, out_must23, stream));
+}
+
+int utf8_last_error(void) { return tl_status; }
+
+const char* utf8_error_string(int code) {
+  switch (code) {
+    case UTF8_OK: return "ok";
+    case UTF8_ERR_INVALID_ARG: return "invalid argument";
+    case UTF8_ERR_CUDA: return "CUDA error";
+    case UTF8_ERR_TIMEOUT: return "device wait timed out";
+    case UTF8_ERR_BUDGET: return "memory budget exceeded";
+    case UTF8_ERR_NOMEM: return "out of memory";
+    default: return "unknown status";
+  }
+}
+
+int utf8_autotune(int flags) {
+  DeviceState* d = device();
+  if (!d) return UTF8_ERR_CUDA;
+  return set_status(run_autotune(flags));
+}
+
+int utf8_tune_cache_load(const char* path) {
+  if (path == nullptr) return set_status(UTF8_ERR_INVALID_ARG);
+  return set_status(tune_cache_load(path));
+}
+
+int utf8_tune_cache_save(const char* path) {
+  if (path == nullptr) return set_status(UTF8_ERR_INVALID_ARG);
+  return set_status(tune_cache_save(path));
+}
+
+int utf8_config_json(char* buf, size_t cap) {
+  DeviceState* d = device();
+  if (!d) return -1;
+  char tmp[256];
+  const int n = snprintf(tmp, sizeof tmp,
+                         "{\"rows\": %d, \"blocks_per_sm\": %d, \"batch_rows\": %d, "
+                         "\"batch_blocks_per_sm\": %d, \"sm_count\": %d}",
+                         d->cfg.rows, d->cfg.blocks_per_sm, d->cfg.batch_rows,
+                         d->cfg.batch_blocks_per_sm, d->sm_count);
+  if (buf != nullptr && cap > 0) {
+    strncpy(buf, tmp, cap - 1);
+    buf[cap - 1] = 0;
+  }
+  set_status(UTF8_OK);
+  return n;
+}
+
+}  // extern "C"

@@ -1,0 +1,233 @@
+// Batched validation: one flag per string, all strings in one launch.
+//
+// The strings of a batch lie back to back in one buffer (string i is
+// data[offsets[i] .. offsets[i+1])).  Instead of scheduling strings, the
+// kernel streams the whole region [offsets[0], offsets[count]) exactly like
+// a single buffer (same tiles, same warp routine, same persistent grid), so
+// every warp gets the same number of bytes whatever the length mix, all lanes
+// stay busy on short strings, and long strings are split across warps with
+// the 3-byte halo stitched through the carried previous word.
+//
+// Streaming the concatenation checks every position with the previous bytes
+// of the concatenation.  That is exact for every position at least three
+// bytes after a string's start (its window lies inside the string).  The
+// positions near string boundaries are checked separately and exactly, one
+// lane per boundary, from the string's own bytes with the virtual zeros the
+// paper puts before and after a stream (Section 6, Section 6.3):
+//   head check of string j: positions o_j .. o_j+3, previous bytes zero,
+//                           bytes past the string's end zero;
+//   tail check of string j: positions e_j .. e_j+3 (all virtual zeros),
+//                           previous bytes the string's last bytes.
+// A streamed error at position p is charged to the string holding p, unless
+// p lies in that string's first three bytes (the head check decides those).
+// Boundary o_j is handled by the warp whose tile holds its position, so each
+// is handled once; flags only ever go from 1 (set before the launch) to 0.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+#include "tune.h"
+#include "lookup.cuh"
+#include "tiles.cuh"
+
+namespace utf8gpu {
+
+// Bytes [x, x + 4) of `data` (absolute offsets), zero outside [lo, hi).
+__device__ __forceinline__ uint32_t gather4(const uint8_t* data, int64_t x, int64_t lo,
+                                            int64_t hi) {
+  uint32_t w = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int64_t y = x + k;
+    if (y >= lo && y < hi) w |= (uint32_t)__ldg(data + y) << (8 * k);
+  }
+  return w;
+}
+
+// First j in [lo, hi) with offsets[j] >= target (hi if none); whole warp.
+__device__ int64_t warp_lower_bound(const int64_t* offsets, int64_t lo, int64_t hi,
+                                    int64_t target) {
+  const int lane = threadIdx.x & (kLanes - 1);
+  while (hi - lo > kLanes) {
+    const int64_t step = (hi - lo + kLanes - 1) / kLanes;
+    const int64_t j = lo + lane * step;
+    const bool ge = j < hi ? offsets[j] >= target : true;
+    const unsigned b = __ballot_sync(kFull, ge);
+    const int f = __ffs(b) - 1;  // b != 0: the lane with j >= hi (or the last) is true
+    const int64_t nhi = lo + (int64_t)f * step < hi ? lo + (int64_t)f * step : hi;
+    const int64_t nlo = f == 0 ? lo : lo + (int64_t)(f - 1) * step + 1;
+    lo = nlo;
+    hi = nhi;
+  }
+  const int64_t j = lo + lane;
+  const bool ge = j < hi ? offsets[j] >= target : true;
+  const unsigned b = __ballot_sync(kFull, ge);
+  const int64_t r = lo + (__ffs(b) - 1);
+  return r < hi ? r : hi;
+}
+
+// Last j in [lo, hi) with offsets[j] <= p, or lo - 1; one thread.
+__device__ __forceinline__ int64_t owner_of(const int64_t* offsets, int64_t lo, int64_t hi,
+                                            int64_t p) {
+  int64_t a = lo - 1, b = hi;  // offsets[a] <= p (virtually), offsets[b] > p (virtually)
+  while (b - a > 1) {
+    const int64_t m = a + (b - a) / 2;
+    if (offsets[m] <= p) a = m; else b = m;
+  }
+  return a;
+}
+
+template <int ROWS>
+__global__ void __launch_bounds__(kBlockThreads)
+    batch_kernel(const uint8_t* __restrict__ data, const int64_t* __restrict__ offsets,
+                 int64_t count, uint8_t* __restrict__ out_valid) {
+  constexpr uint64_t kTileBytes = (uint64_t)kLanes * ROWS * 16;
+  // The region [offsets[0], offsets[count]) is read on the device, so the
+  // launch needs nothing from the host but the pointers (graph capturable).
+  const int64_t o_first = offsets[0];
+  const int64_t o_last = offsets[count];
+  const Span region = make_span(data + o_first, o_last > o_first ? (uint64_t)(o_last - o_first) : 0);
+  const uint64_t tiles = span_tiles<ROWS>(region);
+  const int lane = threadIdx.x & (kLanes - 1);
+  const int left = (lane + kLanes - 1) & (kLanes - 1);
+  const uint64_t warps = (uint64_t)gridDim.x * (kBlockThreads / kLanes);
+  const uint64_t w = (uint64_t)blockIdx.x * (kBlockThreads / kLanes) + (threadIdx.x / kLanes);
+  const uint64_t t0 = tiles * w / warps;
+  const uint64_t t1 = tiles * (w + 1) / warps;
+  if (t0 >= t1) return;
+
+  // absolute offset of virtual position 0 of the region
+  const int64_t vbase = o_first - (int64_t)region.off;
+  // next boundary to handle: the first j with offsets[j] >= start of tile t0
+  int64_t bi = warp_lower_bound(offsets, 0, count + 1, vbase + (int64_t)(t0 * kTileBytes));
+
+  WordLut carry = ascii_lut();
+  if (t0 > 0) carry = lut_word(load_word(region, t0 * kTileBytes - 4));
+
+  for (uint64_t t = t0; t < t1; ++t) {
+    const uint64_t g0 = t * (uint64_t)(kLanes * ROWS);
+    const int64_t tile_lo = vbase + (int64_t)(t * kTileBytes);
+    const int64_t tile_hi = tile_lo + (int64_t)kTileBytes;
+
+    // ---- stream the tile (plain `lookup` over the concatenation) ----------
+    uint4 d[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) d[r] = load_granule(region, g0 + r * kLanes + lane);
+    uint32_t high = 0;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) high |= d[r].x | d[r].y | d[r].z | d[r].w;
+
+    uint32_t e[ROWS][4];
+    uint32_t any_err = 0;
+    if (!__any_sync(kFull, high & 0x80808080u)) {
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) e[r][0] = e[r][1] = e[r][2] = e[r][3] = 0;
+      if (lane == 0) e[0][0] = word_error(carry, lut_word(d[0].x));
+      any_err = e[0][0];
+      carry = ascii_lut();
+    } else {
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        WordLut l0, l1, l2, l3;
+        lut_pair(d[r].x, d[r].y, l0, l1);
+        lut_pair(d[r].z, d[r].w, l2, l3);
+        const WordLut from_left = shfl_lut<kLanes>(l3, left);
+        WordLut prev = from_left;
+        if (lane == 0) prev = carry;
+        carry = from_left;
+        e[r][0] = word_error(prev, l0);
+        e[r][1] = word_error(l0, l1);
+        e[r][2] = word_error(l1, l2);
+        e[r][3] = word_error(l2, l3);
+        any_err |= e[r][0] | e[r][1] | e[r][2] | e[r][3];
+      }
+    }
+
+    // ---- boundaries inside this tile: exact head and tail checks ---------
+    const int64_t bi_tile = bi;
+    for (;;) {
+      const int64_t j = bi + lane;
+      const int64_t oj = j <= count ? offsets[j] : INT64_MAX;
+      const bool in = oj < tile_hi;
+      if (in) {
+        if (j >= 1) {  // tail of string j-1, which ends at oj
+          const int64_t s = offsets[j - 1];
+          const WordLut last = lut_word(gather4(data, oj - 4, s, oj));
+          if (word_error(last, ascii_lut()) != 0) out_valid[j - 1] = 0;
+        }
+        if (j < count) {  // head of string j, which starts at oj
+          const int64_t end = offsets[j + 1];
+          const WordLut first = lut_word(gather4(data, oj, oj, end));
+          if (word_error(ascii_lut(), first) != 0) out_valid[j] = 0;
+        }
+      }
+      const int n_in = __popc(__ballot_sync(kFull, in));
+      bi += n_in;
+      if (n_in < kLanes) break;
+    }
+
+    // ---- charge streamed errors to strings (only where errors exist) -----
+    if (__any_sync(kFull, any_err != 0)) {
+      // strings overlapping the tile: indices bi_tile - 1 .. bi - 1
+      const int64_t lo = bi_tile > 0 ? bi_tile - 1 : 0;
+      const int64_t hi = bi < count ? bi : count;  // owners are < count
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          uint32_t m = e[r][k];
+          while (m != 0) {
+            const int byte = (__ffs(m) - 1) >> 3;
+            m &= ~(0xFFu << (8 * byte));
+            const int64_t p = tile_lo + (int64_t)(r * kLanes + lane) * 16 + 4 * k + byte;
+            const int64_t own = owner_of(offsets, lo, hi + 1, p);
+            if (own >= 0 && own < count && p - offsets[own] >= 3 && p < offsets[own + 1])
+              out_valid[own] = 0;
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int ROWS>
+static cudaError_t launch_batch_rows(const uint8_t* data, const int64_t* offsets, int64_t count,
+                                     uint8_t* out_valid, int blocks_per_sm, int sm_count,
+                                     cudaStream_t st) {
+  const unsigned grid = (unsigned)(sm_count * blocks_per_sm);
+  batch_kernel<ROWS><<<grid, kBlockThreads, 0, st>>>(data, offsets, count, out_valid);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const uint8_t* data, const int64_t* offsets, int64_t count,
+                         uint8_t* out_valid, const LaunchCfg& cfg, int sm_count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(out_valid, 1, (size_t)count, st);
+  if (e != cudaSuccess) return e;
+  switch (cfg.batch_rows) {
+    case 1: return launch_batch_rows<1>(data, offsets, count, out_valid, cfg.batch_blocks_per_sm,
+                                        sm_count, st);
+    case 4: return launch_batch_rows<4>(data, offsets, count, out_valid, cfg.batch_blocks_per_sm,
+                                        sm_count, st);
+    default: return launch_batch_rows<2>(data, offsets, count, out_valid, cfg.batch_blocks_per_sm,
+                                         sm_count, st);
+  }
+}
+
+}  // namespace utf8gpu
+
+namespace utf8gpu {
+
+int batch_blocks_per_sm(int rows) {
+  int n = 0;
+  cudaError_t e;
+  switch (rows) {
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<1>, kBlockThreads, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<4>, kBlockThreads, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<2>, kBlockThreads, 0); break;
+  }
+  if (e != cudaSuccess) { cudaGetLastError(); return 1; }
+  return n > 0 ? n : 1;
+}
+
+}  // namespace utf8gpu

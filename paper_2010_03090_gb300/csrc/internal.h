@@ -1,0 +1,35 @@
+// Internal declarations shared by the kernels and the C-ABI layer.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace utf8gpu {
+
+constexpr int kBlockThreads = 256;
+
+// Launch configuration (picked by the autotuner, or the defaults below).
+struct LaunchCfg {
+  int rows = 4;           // tile rows per warp (tile = rows * 512 bytes): 2, 4 or 8
+  int blocks_per_sm = 8;  // resident CTAs per SM in the persistent grid
+  int batch_rows = 2;     // tile rows for the batch kernel
+  int batch_blocks_per_sm = 8;
+};
+
+cudaError_t launch_validate(const uint8_t* data, uint64_t n, uint8_t* out_valid,
+                            const LaunchCfg& cfg, int sm_count, cudaStream_t st);
+
+// Checks virtual tiles [t_begin, t_end) of a buffer (used for chunked copies:
+// the whole buffer is one stream, chunks arrive over time).  The result byte
+// must have been set to 1 by the caller.
+cudaError_t launch_validate_tiles(const uint8_t* data, uint64_t n, uint64_t t_begin,
+                                  uint64_t t_end, uint8_t* out_valid, const LaunchCfg& cfg,
+                                  int sm_count, cudaStream_t st);
+uint64_t tile_bytes(const LaunchCfg& cfg);
+
+cudaError_t launch_classify_debug(const uint8_t* data, uint64_t n, uint8_t* out_special,
+                                  uint8_t* out_must23, cudaStream_t st);
+
+cudaError_t launch_batch(const uint8_t* data, const int64_t* offsets, int64_t count,
+                         uint8_t* out_valid, const LaunchCfg& cfg, int sm_count, cudaStream_t st);
+
+}  // namespace utf8gpu

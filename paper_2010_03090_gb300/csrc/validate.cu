@@ -1,0 +1,114 @@
+// Single-buffer validation kernel and the classification debug kernel.
+//
+// validate_kernel: a persistent grid (a multiple of the SM count) whose warps
+// each take one contiguous run of tiles of the buffer (Section 6's loop, one
+// loop per warp, the previous block carried in registers), OR their error
+// words and clear the result byte if any lane saw an error.  The result byte
+// is set to 1 beforehand on the same stream.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+#include "tune.h"
+#include "lookup.cuh"
+#include "tiles.cuh"
+
+namespace utf8gpu {
+
+// Tiles [t_first, t_first + tiles) are split into one contiguous run per warp.
+template <int ROWS>
+__global__ void __launch_bounds__(kBlockThreads) validate_kernel(Span s, uint64_t t_first,
+                                                                uint64_t tiles,
+                                                                uint8_t* out_valid) {
+  const uint64_t warps = (uint64_t)gridDim.x * (kBlockThreads / kLanes);
+  const uint64_t w = (uint64_t)blockIdx.x * (kBlockThreads / kLanes) + (threadIdx.x / kLanes);
+  const uint64_t t0 = t_first + tiles * w / warps;
+  const uint64_t t1 = t_first + tiles * (w + 1) / warps;
+  const uint32_t err = warp_check_tiles<ROWS>(s, t0, t1);
+  if (__any_sync(kFull, err != 0) && (threadIdx.x & (kLanes - 1)) == 0) *out_valid = 0;
+}
+
+// One thread per 4-byte word of the virtual layout.
+__global__ void classify_debug_kernel(Span s, uint8_t* out_special, uint8_t* out_must23) {
+  const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t words = s.granules * 4;
+  if (k >= words) return;
+  const WordLut prev = k == 0 ? ascii_lut() : lut_word(load_word(s, 4 * k - 4));
+  const WordLut cur = lut_word(load_word(s, 4 * k));
+  const uint32_t sc = special_cases(prev, cur);
+  const uint32_t m = must_be_2_3(prev, cur);
+  for (int j = 0; j < 4; ++j) {
+    const uint64_t v = 4 * k + j;  // virtual position; output index v - off
+    if (v < s.off || v >= s.off + s.n + 3) continue;
+    out_special[v - s.off] = (uint8_t)(sc >> (8 * j));
+    out_must23[v - s.off] = (uint8_t)(m >> (8 * j));
+  }
+}
+
+template <int ROWS>
+static cudaError_t launch_rows(const Span& s, uint64_t t_begin, uint64_t t_end,
+                               uint8_t* out_valid, const LaunchCfg& cfg, int sm_count,
+                               cudaStream_t st) {
+  const uint64_t all = span_tiles<ROWS>(s);
+  if (t_end > all) t_end = all;
+  if (t_begin >= t_end) return cudaSuccess;
+  const uint64_t tiles = t_end - t_begin;
+  const uint64_t warps_per_block = kBlockThreads / kLanes;
+  uint64_t grid = (uint64_t)sm_count * (uint64_t)cfg.blocks_per_sm;
+  const uint64_t need = (tiles + warps_per_block - 1) / warps_per_block;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  validate_kernel<ROWS><<<(unsigned)grid, kBlockThreads, 0, st>>>(s, t_begin, tiles, out_valid);
+  return cudaGetLastError();
+}
+
+uint64_t tile_bytes(const LaunchCfg& cfg) {
+  const int rows = (cfg.rows == 2 || cfg.rows == 8) ? cfg.rows : 4;
+  return (uint64_t)rows * kLanes * 16;
+}
+
+cudaError_t launch_validate_tiles(const uint8_t* data, uint64_t n, uint64_t t_begin,
+                                  uint64_t t_end, uint8_t* out_valid, const LaunchCfg& cfg,
+                                  int sm_count, cudaStream_t st) {
+  const Span s = make_span(data, n);
+  switch (cfg.rows) {
+    case 2: return launch_rows<2>(s, t_begin, t_end, out_valid, cfg, sm_count, st);
+    case 8: return launch_rows<8>(s, t_begin, t_end, out_valid, cfg, sm_count, st);
+    default: return launch_rows<4>(s, t_begin, t_end, out_valid, cfg, sm_count, st);
+  }
+}
+
+cudaError_t launch_validate(const uint8_t* data, uint64_t n, uint8_t* out_valid,
+                            const LaunchCfg& cfg, int sm_count, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out_valid, 1, 1, st);
+  if (e != cudaSuccess) return e;
+  return launch_validate_tiles(data, n, 0, ~uint64_t(0), out_valid, cfg, sm_count, st);
+}
+
+cudaError_t launch_classify_debug(const uint8_t* data, uint64_t n, uint8_t* out_special,
+                                  uint8_t* out_must23, cudaStream_t st) {
+  const Span s = make_span(data, n);
+  const uint64_t words = s.granules * 4;
+  const unsigned block = 256;
+  const uint64_t grid = (words + block - 1) / block;
+  classify_debug_kernel<<<(unsigned)grid, block, 0, st>>>(s, out_special, out_must23);
+  return cudaGetLastError();
+}
+
+}  // namespace utf8gpu
+
+namespace utf8gpu {
+
+int validate_blocks_per_sm(int rows) {
+  int n = 0;
+  cudaError_t e;
+  switch (rows) {
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, validate_kernel<2>, kBlockThreads, 0); break;
+    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, validate_kernel<8>, kBlockThreads, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, validate_kernel<4>, kBlockThreads, 0); break;
+  }
+  if (e != cudaSuccess) { cudaGetLastError(); return 1; }
+  return n > 0 ? n : 1;
+}
+
+}  // namespace utf8gpu

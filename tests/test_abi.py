@@ -1,0 +1,52 @@
+"""The C-ABI library builds, loads and exports every symbol that
+include/utf8gpu.h declares (CPU only: no compute calls)."""
+import os
+import re
+import subprocess
+
+import paper_2010_03090_gb300 as u
+from conftest import ROOT
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "utf8gpu.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(utf8_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("utf8_validate", "utf8_validate_batch", "utf8_last_error",
+                     "utf8_error_string", "utf8_autotune", "utf8_tune_cache_load",
+                     "utf8_tune_cache_save"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    path = u.lib_path()
+    u.lib()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT\s+(\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        assert hasattr(u.lib(), n)
+
+
+def test_binding_names_match_header():
+    for n in declared_functions():
+        assert callable(getattr(u, n)), n
+
+
+def test_error_strings():
+    assert u.utf8_error_string(0) == "ok"
+    assert u.utf8_error_string(1) == "invalid argument"
+    assert u.utf8_error_string(2) == "CUDA error"
+    assert u.utf8_error_string(999) == "unknown status"
+
+
+def test_library_links_no_shared_runtime():
+    out = subprocess.run(["readelf", "-d", u.lib_path()], capture_output=True, text=True).stdout
+    assert "libcudart" not in out  # static CUDA runtime: only the driver is needed
+    assert "libtorch" not in out
