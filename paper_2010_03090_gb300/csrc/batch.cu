@@ -28,6 +28,7 @@
 #include "internal.h"
 #include "tune.h"
 #include "lookup.cuh"
+#include "search.cuh"
 #include "tiles.cuh"
 
 namespace utf8gpu {
@@ -49,32 +50,16 @@ __device__ int64_t warp_lower_bound(const int64_t* offsets, int64_t lo, int64_t 
                                     int64_t target) {
   const int lane = threadIdx.x & (kLanes - 1);
   while (hi - lo > kLanes) {
-    const int64_t step = (hi - lo + kLanes - 1) / kLanes;
+    const int64_t step = lb_step(lo, hi);
     const int64_t j = lo + lane * step;
     const bool ge = j < hi ? offsets[j] >= target : true;
-    const unsigned b = __ballot_sync(kFull, ge);
-    const int f = __ffs(b) - 1;  // b != 0: the lane with j >= hi (or the last) is true
-    const int64_t nhi = lo + (int64_t)f * step < hi ? lo + (int64_t)f * step : hi;
-    const int64_t nlo = f == 0 ? lo : lo + (int64_t)(f - 1) * step + 1;
-    lo = nlo;
-    hi = nhi;
+    const LbRange r = lb_narrow(lo, hi, step, __ballot_sync(kFull, ge));
+    lo = r.lo;
+    hi = r.hi;
   }
   const int64_t j = lo + lane;
   const bool ge = j < hi ? offsets[j] >= target : true;
-  const unsigned b = __ballot_sync(kFull, ge);
-  const int64_t r = lo + (__ffs(b) - 1);
-  return r < hi ? r : hi;
-}
-
-// Last j in [lo, hi) with offsets[j] <= p, or lo - 1; one thread.
-__device__ __forceinline__ int64_t owner_of(const int64_t* offsets, int64_t lo, int64_t hi,
-                                            int64_t p) {
-  int64_t a = lo - 1, b = hi;  // offsets[a] <= p (virtually), offsets[b] > p (virtually)
-  while (b - a > 1) {
-    const int64_t m = a + (b - a) / 2;
-    if (offsets[m] <= p) a = m; else b = m;
-  }
-  return a;
+  return lb_final(lo, hi, __ballot_sync(kFull, ge));
 }
 
 template <int ROWS>
@@ -180,7 +165,7 @@ __global__ void __launch_bounds__(kBlockThreads)
             const int byte = (__ffs(m) - 1) >> 3;
             m &= ~(0xFFu << (8 * byte));
             const int64_t p = tile_lo + (int64_t)(r * kLanes + lane) * 16 + 4 * k + byte;
-            const int64_t own = owner_of(offsets, lo, hi + 1, p);
+            const int64_t own = last_at_most(offsets, lo, hi + 1, p);
             if (own >= 0 && own < count && p - offsets[own] >= 3 && p < offsets[own + 1])
               out_valid[own] = 0;
           }
