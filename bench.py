@@ -53,6 +53,10 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--buffer-bytes", type=int, default=GIB)
     ap.add_argument("--no-extras", action="store_true", help="skip batch/serving extras")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-memory leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
+    ap.add_argument("--variants", default="ascii,latin,cjk,emoji,uniform",
+                    help="comma-separated subset of the content variants (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="CPU budget of the oracle baseline sample")
     return ap.parse_args()
@@ -79,11 +83,13 @@ def char_start(buf: np.ndarray, p: int) -> int:
     return p
 
 
-def make_workload(n: int, rank: int):
+def make_workload(n: int, rank: int, variants=None):
     """Host arrays of the ten buffers (five clean variants, five tail-error)."""
     import synth
     bufs, names = [], []
     for i, name in enumerate(synth.VARIANTS_1GIB):
+        if variants is not None and name not in variants:
+            continue
         seed = synth.SEED_BASE + 1000 + i + 100 * rank
         clean = synth.fill_variant(n, name, seed)
         bad = clean.copy()
@@ -254,7 +260,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         dist.init_process_group("nccl")
 
     n = args.buffer_bytes
-    host, names = make_workload(n, rank)
+    host, names = make_workload(n, rank, args.variants.split(","))
     dev = [torch.from_numpy(b).cuda() for b in host]
     res = torch.empty(len(dev), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.Stream()
@@ -316,20 +322,22 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     cfg = json.loads(u.utf8_config_json())
 
     # end to end: host buffers through the public host-memory entry point
-    e2e_steps = max(2, min(args.steps, 5))
-    pinned = []
-    for b in host:
-        p = torch.empty(b.size, dtype=torch.uint8, pin_memory=True)
-        p.numpy()[:] = b
-        pinned.append(p)
-    u.utf8_validate_host(pinned[0][: 1 << 20], stream=stream)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_flags = [u.utf8_validate_host(p, stream=stream) for p in pinned]
-    e2e_dt = time.perf_counter() - t
-    e2e_value = bytes_per_step * e2e_steps / e2e_dt / 1e9
-    del pinned
+    e2e_steps = 0 if args.no_e2e else max(2, min(args.steps, 5))
+    e2e_value, e2e_flags = None, flags
+    if e2e_steps:
+        pinned = []
+        for b in host:
+            p = torch.empty(b.size, dtype=torch.uint8, pin_memory=True)
+            p.numpy()[:] = b
+            pinned.append(p)
+        u.utf8_validate_host(pinned[0][: 1 << 20], stream=stream)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_flags = [u.utf8_validate_host(p, stream=stream) for p in pinned]
+        e2e_dt = time.perf_counter() - t
+        e2e_value = bytes_per_step * e2e_steps / e2e_dt / 1e9
+        del pinned
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
@@ -350,14 +358,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                      "algorithmic_bytes_per_launch": n},
         "per_variant_gbs": per_variant,
         "flags": dict(zip(names, flags)),
-        "e2e": {"value": round(e2e_value, 1), "unit": "GB/s",
+        "e2e": {"value": round(e2e_value, 1) if e2e_value else None, "unit": "GB/s",
                 "h2d_bytes_per_step": bytes_per_step, "d2h_bytes_per_step": len(host),
                 "steps": e2e_steps, "api": "utf8_validate_host (pinned host buffers)",
                 "flags_ok": [bool(f) for f in e2e_flags] == [bool(f) for f in flags]},
         "gpu_launches": len(dev) * args.steps,
         "clocks": clock_info,
     }
-    if world == 1:
+    if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = oracle_baseline(host, names, args.cpu_seconds)
     if not args.no_extras and world == 1:
         del dev

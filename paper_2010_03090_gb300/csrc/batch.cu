@@ -74,7 +74,6 @@ __global__ void __launch_bounds__(kBlockThreads)
   const Span region = make_span(data + o_first, o_last > o_first ? (uint64_t)(o_last - o_first) : 0);
   const uint64_t tiles = span_tiles<ROWS>(region);
   const int lane = threadIdx.x & (kLanes - 1);
-  const int left = (lane + kLanes - 1) & (kLanes - 1);
   const uint64_t warps = (uint64_t)gridDim.x * (kBlockThreads / kLanes);
   const uint64_t w = (uint64_t)blockIdx.x * (kBlockThreads / kLanes) + (threadIdx.x / kLanes);
   const uint64_t t0 = tiles * w / warps;
@@ -88,45 +87,23 @@ __global__ void __launch_bounds__(kBlockThreads)
 
   WordLut carry = ascii_lut();
   if (t0 > 0) carry = lut_word(load_word(region, t0 * kTileBytes - 4));
+  uint64_t in0, in1;
+  interior_tiles<ROWS>(region, in0, in1);
+  const uint8_t* lane_ptr = region.abase + t0 * kTileBytes + lane * 16;
 
-  for (uint64_t t = t0; t < t1; ++t) {
-    const uint64_t g0 = t * (uint64_t)(kLanes * ROWS);
+  for (uint64_t t = t0; t < t1; ++t, lane_ptr += kTileBytes) {
     const int64_t tile_lo = vbase + (int64_t)(t * kTileBytes);
     const int64_t tile_hi = tile_lo + (int64_t)kTileBytes;
 
     // ---- stream the tile (plain `lookup` over the concatenation) ----------
     uint4 d[ROWS];
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r) d[r] = load_granule(region, g0 + r * kLanes + lane);
-    uint32_t high = 0;
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r) high |= d[r].x | d[r].y | d[r].z | d[r].w;
-
+    if (t >= in0 && t < in1) load_tile_interior<ROWS>(lane_ptr, d);
+    else load_tile_checked<ROWS>(region, t, lane, d);
     uint32_t e[ROWS][4];
+    check_tile<ROWS>(d, carry, lane, e);
     uint32_t any_err = 0;
-    if (!__any_sync(kFull, high & 0x80808080u)) {
 #pragma unroll
-      for (int r = 0; r < ROWS; ++r) e[r][0] = e[r][1] = e[r][2] = e[r][3] = 0;
-      if (lane == 0) e[0][0] = word_error(carry, lut_word(d[0].x));
-      any_err = e[0][0];
-      carry = ascii_lut();
-    } else {
-#pragma unroll
-      for (int r = 0; r < ROWS; ++r) {
-        WordLut l0, l1, l2, l3;
-        lut_pair(d[r].x, d[r].y, l0, l1);
-        lut_pair(d[r].z, d[r].w, l2, l3);
-        const WordLut from_left = shfl_lut<kLanes>(l3, left);
-        WordLut prev = from_left;
-        if (lane == 0) prev = carry;
-        carry = from_left;
-        e[r][0] = word_error(prev, l0);
-        e[r][1] = word_error(l0, l1);
-        e[r][2] = word_error(l1, l2);
-        e[r][3] = word_error(l2, l3);
-        any_err |= e[r][0] | e[r][1] | e[r][2] | e[r][3];
-      }
-    }
+    for (int r = 0; r < ROWS; ++r) any_err |= e[r][0] | e[r][1] | e[r][2] | e[r][3];
 
     // ---- boundaries inside this tile: exact head and tail checks ---------
     const int64_t bi_tile = bi;

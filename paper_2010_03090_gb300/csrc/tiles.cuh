@@ -94,82 +94,102 @@ __device__ __forceinline__ uint32_t load_word(const Span& s, uint64_t v) {
   return w & keep_bytes(a, b);
 }
 
-template <int GROUP>
 __device__ __forceinline__ WordLut shfl_lut(const WordLut& l, int src) {
   WordLut r;
-  r.prev_side = __shfl_sync(kFull, l.prev_side, src, GROUP);
+  r.prev_side = __shfl_sync(kFull, l.prev_side, src);
   r.cur_side = 0;  // a left neighbour only ever serves as "previous"
-  r.flags = __shfl_sync(kFull, l.flags, src, GROUP);
+  r.flags = __shfl_sync(kFull, l.flags, src);
   return r;
 }
 
-// Checks tiles [t_begin, t_end) of a stream with a group of GROUP lanes
-// (GROUP = 8, 16 or 32; the 32 / GROUP groups of a warp each have their own
-// stream and range).  A tile is ROWS rows of GROUP lanes x 16 bytes.  All
-// groups run `trip` iterations (trip >= t_end - t_begin of every group) so
-// that warp-wide shuffles and votes stay converged; a group whose range is
-// exhausted idles.  Returns a non-zero value in some lane of the group iff
-// an error lies in the group's tiles.  Call with the whole warp.
-template <int ROWS, int GROUP>
-__device__ __forceinline__ uint32_t group_check_tiles(const Span& s, uint64_t t_begin,
-                                                      uint64_t t_end, uint64_t trip) {
-  constexpr uint64_t kTileGranules = (uint64_t)GROUP * ROWS;
-  const int lane = threadIdx.x & (kLanes - 1);
-  const int glane = lane & (GROUP - 1);
-  const int left = (glane + GROUP - 1) & (GROUP - 1);
-  const unsigned gmask = GROUP == 32 ? kFull : (((1u << GROUP) - 1u) << (lane & ~(GROUP - 1)));
-  uint32_t err = 0;
-  WordLut carry = ascii_lut();  // lookups of the 4 bytes before the row (group lane 0)
-  if (t_begin < t_end && t_begin > 0)
-    carry = lut_word(load_word(s, t_begin * kTileGranules * 16 - 4));
+template <int ROWS>
+struct TileGeom {
+  static constexpr uint64_t kGranules = (uint64_t)kLanes * ROWS;
+  static constexpr uint64_t kBytes = kGranules * 16;
+};
 
-  for (uint64_t i = 0; i < trip; ++i) {
-    const uint64_t t = t_begin + i;
-    const bool active = t < t_end;
-    const uint64_t g0 = t * kTileGranules;
-    uint4 d[ROWS];
+// Tile t with bounds checks (first and last tiles of a stream).
+template <int ROWS>
+__device__ __forceinline__ void load_tile_checked(const Span& s, uint64_t t, int lane,
+                                                  uint4 (&d)[ROWS]) {
+  const uint64_t g0 = t * TileGeom<ROWS>::kGranules;
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r)
-      d[r] = active ? load_granule(s, g0 + r * GROUP + glane) : make_uint4(0u, 0u, 0u, 0u);
-
-    uint32_t high = 0;
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r) high |= d[r].x | d[r].y | d[r].z | d[r].w;
-    const unsigned nonascii = __ballot_sync(kFull, (high & 0x80808080u) != 0);
-    if ((nonascii & gmask) == 0) {
-      // All-ASCII tile (Section 6.4): no classification, but the bytes before
-      // the tile must not end inside a character.
-      if (active && glane == 0) err |= word_error(carry, lut_word(d[0].x));
-      carry = ascii_lut();
-    }
-    // The classification runs when any group of the warp needs it; a group
-    // whose tile is ASCII (or idle) computes on its own bytes, harmlessly.
-    if (nonascii != 0) {
-#pragma unroll
-      for (int r = 0; r < ROWS; ++r) {
-        WordLut l0, l1, l2, l3;
-        lut_pair(d[r].x, d[r].y, l0, l1);
-        lut_pair(d[r].z, d[r].w, l2, l3);
-        const WordLut from_left = shfl_lut<GROUP>(l3, left);  // group lane 0 gets the last lane
-        WordLut prev = from_left;
-        if (glane == 0) prev = carry;
-        const uint32_t e =
-            word_error(prev, l0) | word_error(l0, l1) | word_error(l1, l2) | word_error(l2, l3);
-        const bool live = active && (nonascii & gmask) != 0 && g0 + r * GROUP < s.granules;
-        if (live) {
-          err |= e;
-          carry = from_left;
-        }
-      }
-    }
-  }
-  return err;
+  for (int r = 0; r < ROWS; ++r) d[r] = load_granule(s, g0 + r * kLanes + lane);
 }
 
+// Tile wholly inside the data: lane_ptr = abase + t * tile bytes + lane * 16.
+template <int ROWS>
+__device__ __forceinline__ void load_tile_interior(const uint8_t* lane_ptr, uint4 (&d)[ROWS]) {
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) d[r] = ld_stream(lane_ptr + r * kLanes * 16);
+}
+
+// Interior tiles of a stream: [first, last) (every granule inside [off, off + n)).
+template <int ROWS>
+__device__ __forceinline__ void interior_tiles(const Span& s, uint64_t& first, uint64_t& last) {
+  constexpr uint64_t tb = TileGeom<ROWS>::kBytes;
+  first = (s.off + tb - 1) / tb;
+  last = (s.off + s.n) / tb;
+}
+
+// Checks one loaded tile.  e[r][k] is the error word of word k of row r of
+// this lane (non-zero bytes = error positions); `carry` holds the lookups of
+// the 4 bytes before the tile (meaningful in lane 0) and is updated.
+template <int ROWS>
+__device__ __forceinline__ void check_tile(const uint4 (&d)[ROWS], WordLut& carry, int lane,
+                                           uint32_t (&e)[ROWS][4]) {
+  const int left = (lane + kLanes - 1) & (kLanes - 1);
+  uint32_t high = 0;
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) high |= d[r].x | d[r].y | d[r].z | d[r].w;
+  if (!__any_sync(kFull, high & 0x80808080u)) {
+    // All-ASCII tile (Section 6.4): no classification, but the bytes before
+    // the tile must not end inside a character.
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) e[r][0] = e[r][1] = e[r][2] = e[r][3] = 0;
+    if (lane == 0) e[0][0] = word_error(carry, lut_word(d[0].x));
+    carry = ascii_lut();
+    return;
+  }
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+    WordLut l0, l1, l2, l3;
+    lut_pair(d[r].x, d[r].y, l0, l1);
+    lut_pair(d[r].z, d[r].w, l2, l3);
+    const WordLut from_left = shfl_lut(l3, left);  // lane 0 receives lane 31
+    WordLut prev = from_left;
+    if (lane == 0) prev = carry;
+    carry = from_left;
+    e[r][0] = word_error(prev, l0);
+    e[r][1] = word_error(l0, l1);
+    e[r][2] = word_error(l1, l2);
+    e[r][3] = word_error(l2, l3);
+  }
+}
+
+// Checks tiles [t_begin, t_end) of a stream with one warp; returns a non-zero
+// value in some lane iff an error lies in those tiles.
 template <int ROWS>
 __device__ __forceinline__ uint32_t warp_check_tiles(const Span& s, uint64_t t_begin,
                                                      uint64_t t_end) {
-  return group_check_tiles<ROWS, 32>(s, t_begin, t_end, t_end > t_begin ? t_end - t_begin : 0);
+  constexpr uint64_t tb = TileGeom<ROWS>::kBytes;
+  const int lane = threadIdx.x & (kLanes - 1);
+  uint32_t err = 0;
+  WordLut carry = ascii_lut();  // zeros before the stream
+  if (t_begin < t_end && t_begin > 0) carry = lut_word(load_word(s, t_begin * tb - 4));
+  uint64_t in0, in1;
+  interior_tiles<ROWS>(s, in0, in1);
+  const uint8_t* lane_ptr = s.abase + t_begin * tb + lane * 16;
+  for (uint64_t t = t_begin; t < t_end; ++t, lane_ptr += tb) {
+    uint4 d[ROWS];
+    if (t >= in0 && t < in1) load_tile_interior<ROWS>(lane_ptr, d);
+    else load_tile_checked<ROWS>(s, t, lane, d);
+    uint32_t e[ROWS][4];
+    check_tile<ROWS>(d, carry, lane, e);
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) err |= e[r][0] | e[r][1] | e[r][2] | e[r][3];
+  }
+  return err;
 }
 
 }  // namespace utf8gpu
