@@ -85,8 +85,9 @@ __global__ void __launch_bounds__(kBlockThreads)
   // next boundary to handle: the first j with offsets[j] >= start of tile t0
   int64_t bi = warp_lower_bound(offsets, 0, count + 1, vbase + (int64_t)(t0 * kTileBytes));
 
-  WordLut carry = ascii_lut();
-  if (t0 > 0) carry = lut_word(load_word(region, t0 * kTileBytes - 4));
+  const uint32_t merge_sel = carry_merge_selector(lane);
+  Carry carry = ascii_carry();
+  if (t0 > 0) carry = halo_carry(load_word(region, t0 * kTileBytes - 4));
   uint64_t in0, in1;
   interior_tiles<ROWS>(region, in0, in1);
   const uint8_t* lane_ptr = region.abase + t0 * kTileBytes + lane * 16;
@@ -99,11 +100,13 @@ __global__ void __launch_bounds__(kBlockThreads)
     uint4 d[ROWS];
     if (t >= in0 && t < in1) load_tile_interior<ROWS>(lane_ptr, d);
     else load_tile_checked<ROWS>(region, t, lane, d);
-    uint32_t e[ROWS][4];
-    check_tile<ROWS>(d, carry, lane, e);
+    uint32_t e[ROWS / 2][8];
+    check_tile<ROWS>(d, carry, lane, merge_sel, e);
     uint32_t any_err = 0;
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) any_err |= e[r][0] | e[r][1] | e[r][2] | e[r][3];
+    for (int p = 0; p < ROWS / 2; ++p)
+#pragma unroll
+      for (int m = 0; m < 8; ++m) any_err |= e[p][m];
 
     // ---- boundaries inside this tile: exact head and tail checks ---------
     const int64_t bi_tile = bi;
@@ -134,14 +137,14 @@ __global__ void __launch_bounds__(kBlockThreads)
       const int64_t lo = bi_tile > 0 ? bi_tile - 1 : 0;
       const int64_t hi = bi < count ? bi : count;  // owners are < count
 #pragma unroll
-      for (int r = 0; r < ROWS; ++r) {
+      for (int pr = 0; pr < ROWS / 2; ++pr) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          uint32_t m = e[r][k];
-          while (m != 0) {
-            const int byte = (__ffs(m) - 1) >> 3;
-            m &= ~(0xFFu << (8 * byte));
-            const int64_t p = tile_lo + (int64_t)(r * kLanes + lane) * 16 + 4 * k + byte;
+        for (int m = 0; m < 8; ++m) {
+          uint32_t bits = e[pr][m];
+          while (bits != 0) {
+            const int byte = (__ffs(bits) - 1) >> 3;
+            bits &= ~(0xFFu << (8 * byte));
+            const int64_t p = tile_lo + (int64_t)interleaved_position<ROWS>(pr, m, byte, lane);
             const int64_t own = last_at_most(offsets, lo, hi + 1, p);
             if (own >= 0 && own < count && p - offsets[own] >= 3 && p < offsets[own + 1])
               out_valid[own] = 0;
@@ -167,8 +170,6 @@ cudaError_t launch_batch(const uint8_t* data, const int64_t* offsets, int64_t co
   cudaError_t e = cudaMemsetAsync(out_valid, 1, (size_t)count, st);
   if (e != cudaSuccess) return e;
   switch (cfg.batch_rows) {
-    case 1: return launch_batch_rows<1>(data, offsets, count, out_valid, cfg.batch_blocks_per_sm,
-                                        sm_count, st);
     case 4: return launch_batch_rows<4>(data, offsets, count, out_valid, cfg.batch_blocks_per_sm,
                                         sm_count, st);
     default: return launch_batch_rows<2>(data, offsets, count, out_valid, cfg.batch_blocks_per_sm,
@@ -184,7 +185,6 @@ int batch_blocks_per_sm(int rows) {
   int n = 0;
   cudaError_t e;
   switch (rows) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<1>, kBlockThreads, 0); break;
     case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<4>, kBlockThreads, 0); break;
     default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<2>, kBlockThreads, 0); break;
   }

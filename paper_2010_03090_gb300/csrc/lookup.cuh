@@ -110,11 +110,11 @@ struct WordLut {
 };
 
 // Table lookups for one word, given its packed selectors.
-//   hi_c : complemented high nibbles in bits 0..15
-//   lo   : low nibbles, lo_c: complemented low nibbles, in bits 0..15
-__device__ __forceinline__ WordLut lut_from_selectors(uint32_t word, uint32_t hi_c, uint32_t lo,
+//   nonascii : 0xFF in each byte whose byte value has its msb set
+//   hi_c     : complemented high nibbles in bits 0..15
+//   lo, lo_c : low nibbles and their complements in bits 0..15
+__device__ __forceinline__ WordLut lut_from_selectors(uint32_t nonascii, uint32_t hi_c, uint32_t lo,
                                                       uint32_t lo_c) {
-  const uint32_t nonascii = prmt(word, 0, 0xBA98);  // 0xFF where the byte's msb is set
   const uint32_t b1h = prmt(kB1H_R0, kB1H_R1, hi_c);
   const uint32_t b2h = prmt(kB2H_R0, kB2H_R1, hi_c);
   const uint32_t b1l = prmt(kB1L_L0, kB1L_L1, lo) & prmt(kB1L_R0, kB1L_R1, lo_c);
@@ -125,7 +125,8 @@ __device__ __forceinline__ WordLut lut_from_selectors(uint32_t word, uint32_t hi
   return r;
 }
 
-// Lookups for two consecutive words c (bytes 0..3) and d (bytes 4..7).
+// Lookups for two consecutive words c (bytes 0..3) and d (bytes 4..7), results
+// in natural byte order.
 __device__ __forceinline__ void lut_pair(uint32_t c, uint32_t d, WordLut& lc, WordLut& ld) {
   const uint32_t u = prmt(c, d, 0x6420);  // c0 c2 d0 d2
   const uint32_t v = prmt(c, d, 0x7531);  // c1 c3 d1 d3
@@ -133,15 +134,29 @@ __device__ __forceinline__ void lut_pair(uint32_t c, uint32_t d, WordLut& lc, Wo
   const uint32_t hi_c = ~(((u >> 4) & 0x0F0F0F0Fu) | (v & 0xF0F0F0F0u));
   const uint32_t lo = (u & 0x0F0F0F0Fu) | ((v << 4) & 0xF0F0F0F0u);
   const uint32_t lo_c = ~lo;
-  lc = lut_from_selectors(c, hi_c, lo, lo_c);
-  ld = lut_from_selectors(d, hi_c >> 16, lo >> 16, lo_c >> 16);
+  lc = lut_from_selectors(prmt(c, 0, 0xBA98), hi_c, lo, lo_c);
+  ld = lut_from_selectors(prmt(d, 0, 0xBA98), hi_c >> 16, lo >> 16, lo_c >> 16);
 }
 
-// Lookups for a single word (used for halo words and debug paths).
+// Lookups for a single word (halo words, boundary checks and the debug path).
 __device__ __forceinline__ WordLut lut_word(uint32_t c) {
   WordLut a, b;
   lut_pair(c, 0, a, b);
   return a;
+}
+
+// Lookups for word c of one stream and word d of another, interleaved:
+//   A = (c0, d0, c1, d1), B = (c2, d2, c3, d3).
+// With two streams side by side a single shift and mask packs the nibble
+// selectors of eight bytes, and the previous bytes of a word are a 16-bit
+// funnel shift (prev1), the previous word itself (prev2) or a 16-bit funnel
+// of the two previous words (prev3).
+__device__ __forceinline__ void lut_interleaved(uint32_t c, uint32_t d, WordLut& A, WordLut& B) {
+  const uint32_t hi_c = ~(((c >> 4) & 0x0F0F0F0Fu) | (d & 0xF0F0F0F0u));
+  const uint32_t lo = (c & 0x0F0F0F0Fu) | ((d << 4) & 0xF0F0F0F0u);
+  const uint32_t lo_c = ~lo;
+  A = lut_from_selectors(prmt(c, d, 0xD9C8), hi_c, lo, lo_c);
+  B = lut_from_selectors(prmt(c, d, 0xFBEA), hi_c >> 16, lo >> 16, lo_c >> 16);
 }
 
 // special_cases (Fig. 1) for the four bytes of a word, given the previous
@@ -156,9 +171,19 @@ __device__ __forceinline__ uint32_t must_be_2_3(const WordLut& prev, const WordL
          kTwoConts;
 }
 
-// Non-zero iff one of the word's four positions is an error.
+// Non-zero iff one of the word's four positions is an error (natural order).
 __device__ __forceinline__ uint32_t word_error(const WordLut& prev, const WordLut& cur) {
   return special_cases(prev, cur) ^ must_be_2_3(prev, cur);
+}
+
+// The same for an interleaved word W_m, given W_{m-1} (p1) and W_{m-2} (p2):
+// prev1 = funnel(W_{m-1}, W_m, 16); prev2 = W_{m-1} (flag bit 6 -> bit 7);
+// prev3 = funnel(W_{m-2}, W_{m-1}, 16) (flag bit 5 -> bit 7, so 18 bits).
+__device__ __forceinline__ uint32_t interleaved_error(const WordLut& p2, const WordLut& p1,
+                                                      const WordLut& cur) {
+  const uint32_t sc = __funnelshift_l(p1.prev_side, cur.prev_side, 16) & cur.cur_side;
+  const uint32_t m = ((p1.flags << 1) | __funnelshift_l(p2.flags, p1.flags, 18)) & kTwoConts;
+  return sc ^ m;
 }
 
 // Lookups of an all-ASCII word (also the zero padding before a stream).

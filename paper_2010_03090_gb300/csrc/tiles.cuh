@@ -94,12 +94,33 @@ __device__ __forceinline__ uint32_t load_word(const Span& s, uint64_t v) {
   return w & keep_bytes(a, b);
 }
 
-__device__ __forceinline__ WordLut shfl_lut(const WordLut& l, int src) {
-  WordLut r;
-  r.prev_side = __shfl_sync(kFull, l.prev_side, src);
-  r.cur_side = 0;  // a left neighbour only ever serves as "previous"
-  r.flags = __shfl_sync(kFull, l.flags, src);
-  return r;
+// What lane 0 of a row pair needs from the row pair before it: the lookups of
+// the last two interleaved words (W_6, W_7) of lane 31, i.e. the last four
+// bytes of both rows.  Only their second-stream bytes (1 and 3) are used.
+struct Carry {
+  uint32_t x7;  // prev_side of W_7
+  uint32_t f7;  // flags of W_7
+  uint32_t f6;  // flags of W_6
+};
+
+__device__ __forceinline__ Carry ascii_carry() {
+  const WordLut a = ascii_lut();
+  return Carry{a.prev_side, a.flags, a.flags};
+}
+
+// Carry for a stream whose previous four bytes (natural order) are `halo`.
+__device__ __forceinline__ Carry halo_carry(uint32_t halo) {
+  const WordLut h = lut_word(halo);
+  return Carry{prmt(h.prev_side, 0, 0x3020), prmt(h.flags, 0, 0x3020), prmt(h.flags, 0, 0x1000)};
+}
+
+// The carry's last four bytes as natural-order lookups (for a word check).
+__device__ __forceinline__ WordLut carry_as_word(const Carry& c) {
+  WordLut w;
+  w.prev_side = c.x7;  // byte 3 = the byte just before
+  w.cur_side = 0;
+  w.flags = prmt(c.f6, c.f7, 0x7531);
+  return w;
 }
 
 template <int ROWS>
@@ -132,12 +153,15 @@ __device__ __forceinline__ void interior_tiles(const Span& s, uint64_t& first, u
   last = (s.off + s.n) / tb;
 }
 
-// Checks one loaded tile.  e[r][k] is the error word of word k of row r of
-// this lane (non-zero bytes = error positions); `carry` holds the lookups of
-// the 4 bytes before the tile (meaningful in lane 0) and is updated.
+// Checks one loaded tile.  Rows 2p and 2p+1 are processed together as two
+// interleaved streams (see lut_interleaved): e[p][m] is the error word of
+// interleaved word W_m = (row 2p byte 2m, row 2p+1 byte 2m, row 2p byte
+// 2m+1, row 2p+1 byte 2m+1) of this lane's granules.  `carry` describes the
+// bytes before the tile (lane 0) and is updated.
 template <int ROWS>
-__device__ __forceinline__ void check_tile(const uint4 (&d)[ROWS], WordLut& carry, int lane,
-                                           uint32_t (&e)[ROWS][4]) {
+__device__ __forceinline__ void check_tile(const uint4 (&d)[ROWS], Carry& carry, int lane,
+                                           uint32_t merge_sel, uint32_t (&e)[ROWS / 2][8]) {
+  static_assert(ROWS % 2 == 0, "rows are processed in pairs");
   const int left = (lane + kLanes - 1) & (kLanes - 1);
   uint32_t high = 0;
 #pragma unroll
@@ -146,25 +170,55 @@ __device__ __forceinline__ void check_tile(const uint4 (&d)[ROWS], WordLut& carr
     // All-ASCII tile (Section 6.4): no classification, but the bytes before
     // the tile must not end inside a character.
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) e[r][0] = e[r][1] = e[r][2] = e[r][3] = 0;
-    if (lane == 0) e[0][0] = word_error(carry, lut_word(d[0].x));
-    carry = ascii_lut();
+    for (int p = 0; p < ROWS / 2; ++p)
+#pragma unroll
+      for (int m = 0; m < 8; ++m) e[p][m] = 0;
+    if (lane == 0) {
+      const uint32_t first = word_error(carry_as_word(carry), lut_word(d[0].x));
+      e[0][0] = prmt(first, 0, 0x4140);  // positions 0, 1 of row 0
+      e[0][1] = prmt(first, 0, 0x4342);  // positions 2, 3 of row 0
+    }
+    carry = ascii_carry();
     return;
   }
 #pragma unroll
-  for (int r = 0; r < ROWS; ++r) {
-    WordLut l0, l1, l2, l3;
-    lut_pair(d[r].x, d[r].y, l0, l1);
-    lut_pair(d[r].z, d[r].w, l2, l3);
-    const WordLut from_left = shfl_lut(l3, left);  // lane 0 receives lane 31
-    WordLut prev = from_left;
-    if (lane == 0) prev = carry;
-    carry = from_left;
-    e[r][0] = word_error(prev, l0);
-    e[r][1] = word_error(l0, l1);
-    e[r][2] = word_error(l1, l2);
-    e[r][3] = word_error(l2, l3);
+  for (int p = 0; p < ROWS / 2; ++p) {
+    const uint4 c = d[2 * p], n = d[2 * p + 1];
+    WordLut W[8];
+    lut_interleaved(c.x, n.x, W[0], W[1]);
+    lut_interleaved(c.y, n.y, W[2], W[3]);
+    lut_interleaved(c.z, n.z, W[4], W[5]);
+    lut_interleaved(c.w, n.w, W[6], W[7]);
+    // left neighbour's W_7, W_6; lane 0 takes its first stream from the carry
+    // (the row before) and its second stream from lane 31 of the first row
+    const uint32_t x7 = __shfl_sync(kFull, W[7].prev_side, left);
+    const uint32_t f7 = __shfl_sync(kFull, W[7].flags, left);
+    const uint32_t f6 = __shfl_sync(kFull, W[6].flags, left);
+    WordLut L7, L6;
+    L7.prev_side = prmt(carry.x7, x7, merge_sel);
+    L7.flags = prmt(carry.f7, f7, merge_sel);
+    L7.cur_side = 0;
+    L6.flags = prmt(carry.f6, f6, merge_sel);
+    L6.prev_side = L6.cur_side = 0;
+    carry = Carry{x7, f7, f6};
+    e[p][0] = interleaved_error(L6, L7, W[0]);
+    e[p][1] = interleaved_error(L7, W[0], W[1]);
+#pragma unroll
+    for (int m = 2; m < 8; ++m) e[p][m] = interleaved_error(W[m - 2], W[m - 1], W[m]);
   }
+}
+
+// Virtual position (relative to the tile start) of byte b of interleaved
+// error word m of row pair p in lane `lane`.
+template <int ROWS>
+__device__ __forceinline__ uint32_t interleaved_position(int p, int m, int b, int lane) {
+  const int row = 2 * p + (b & 1);
+  return (uint32_t)(row * kLanes + lane) * 16u + (uint32_t)(2 * m + (b >> 1));
+}
+
+// Selector merging the carry into lane 0's left neighbour (see check_tile).
+__device__ __forceinline__ uint32_t carry_merge_selector(int lane) {
+  return lane == 0 ? 0x6341u : 0x7654u;
 }
 
 // Checks tiles [t_begin, t_end) of a stream with one warp; returns a non-zero
@@ -175,8 +229,9 @@ __device__ __forceinline__ uint32_t warp_check_tiles(const Span& s, uint64_t t_b
   constexpr uint64_t tb = TileGeom<ROWS>::kBytes;
   const int lane = threadIdx.x & (kLanes - 1);
   uint32_t err = 0;
-  WordLut carry = ascii_lut();  // zeros before the stream
-  if (t_begin < t_end && t_begin > 0) carry = lut_word(load_word(s, t_begin * tb - 4));
+  const uint32_t merge_sel = carry_merge_selector(lane);
+  Carry carry = ascii_carry();  // zeros before the stream
+  if (t_begin < t_end && t_begin > 0) carry = halo_carry(load_word(s, t_begin * tb - 4));
   uint64_t in0, in1;
   interior_tiles<ROWS>(s, in0, in1);
   const uint8_t* lane_ptr = s.abase + t_begin * tb + lane * 16;
@@ -184,10 +239,12 @@ __device__ __forceinline__ uint32_t warp_check_tiles(const Span& s, uint64_t t_b
     uint4 d[ROWS];
     if (t >= in0 && t < in1) load_tile_interior<ROWS>(lane_ptr, d);
     else load_tile_checked<ROWS>(s, t, lane, d);
-    uint32_t e[ROWS][4];
-    check_tile<ROWS>(d, carry, lane, e);
+    uint32_t e[ROWS / 2][8];
+    check_tile<ROWS>(d, carry, lane, merge_sel, e);
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) err |= e[r][0] | e[r][1] | e[r][2] | e[r][3];
+    for (int p = 0; p < ROWS / 2; ++p)
+#pragma unroll
+      for (int m = 0; m < 8; ++m) err |= e[p][m];
   }
   return err;
 }
