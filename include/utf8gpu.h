@@ -97,6 +97,23 @@ int utf8_validate_batch(const uint8_t* data, const int64_t* offsets, int64_t cou
 bool utf8_validate_host(const uint8_t* host_data, size_t len, cudaStream_t stream);
 
 /*
+ * utf8_validate_host without any allocation, for callers that cannot allocate
+ * GPU memory when they validate: services whose GPU memory is reserved up
+ * front by a pool or another framework, latency-critical paths where
+ * cudaMalloc/cudaFree could synchronise the device, code that must keep a
+ * fixed footprint.  The paper has no counterpart; it is a packaging of the
+ * same kernel.  The input (host memory, len <= 32 MiB; longer inputs are
+ * rejected with UTF8_ERR_BUDGET) is staged through a fixed 32 MiB + 4 KiB
+ * array compiled into the library, which every GPU that loads the library
+ * holds until exit.  A device's first call looks up that array's device
+ * address; make it before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU race on it (serialise them).
+ * Synchronous; returns true iff valid, false with utf8_last_error() set
+ * otherwise.
+ */
+bool utf8_validate_host_noalloc(const uint8_t* host_data, size_t len, cudaStream_t stream);
+
+/*
  * Debug view of the classification (Fig. 1 and Section 6.2) of one buffer:
  * for each position i in 0 .. len+2 (the buffer followed by its three zero
  * padding bytes) writes special_cases[i] = byte_1_high & byte_1_low &

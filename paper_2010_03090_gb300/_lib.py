@@ -14,6 +14,7 @@ EXPORTS = (
     "utf8_validate", "utf8_validate_async", "utf8_validate_batch", "utf8_validate_host",
     "utf8_classify_debug", "utf8_last_error", "utf8_error_string", "utf8_autotune",
     "utf8_tune_cache_load", "utf8_tune_cache_save", "utf8_config_json",
+    "utf8_validate_host_noalloc",
 )
 
 
@@ -58,6 +59,8 @@ def lib() -> ctypes.CDLL:
             L.utf8_tune_cache_save.restype = i32
             L.utf8_config_json.argtypes = [ctypes.c_char_p, sz]
             L.utf8_config_json.restype = i32
+            L.utf8_validate_host_noalloc.argtypes = [vp, sz, vp]
+            L.utf8_validate_host_noalloc.restype = ctypes.c_bool
             _lib = L
     return _lib
 
@@ -155,6 +158,19 @@ def utf8_validate_host(host, stream=None) -> bool:
     ok = lib().utf8_validate_host(p or None, n, _stream(stream))
     del keep
     _check(lib().utf8_last_error(), "utf8_validate_host")
+    return bool(ok)
+
+
+def utf8_validate_host_noalloc(host, stream=None) -> bool:
+    """utf8_validate_host for callers that cannot allocate GPU memory: stages
+    through a fixed 32 MiB array inside the library (longer inputs raise with
+    UTF8_ERR_BUDGET).  Calls that overlap on the GPU share that array."""
+    if hasattr(host, "ctypes"):  # numpy
+        p, n = host.ctypes.data, host.nbytes
+    else:  # torch CPU tensor
+        p, n = host.data_ptr(), host.numel() * host.element_size()
+    ok = lib().utf8_validate_host_noalloc(p or None, n, _stream(stream))
+    _check(lib().utf8_last_error(), "utf8_validate_host_noalloc")
     return bool(ok)
 
 

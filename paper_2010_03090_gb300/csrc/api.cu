@@ -107,6 +107,9 @@ int cuda_status(cudaError_t e) { return set_status(e == cudaSuccess ? UTF8_OK : 
 
 }  // namespace
 
+// Status setter for entry points defined in other files.
+int set_thread_status(int status) { return set_status(status); }
+
 LaunchCfg current_config() {
   DeviceState* d = device();
   return d ? d->cfg : LaunchCfg();
