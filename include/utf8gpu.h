@@ -125,6 +125,60 @@ bool utf8_validate_host_noalloc(const uint8_t* host_data, size_t len, cudaStream
 int utf8_classify_debug(const uint8_t* data, size_t len, uint8_t* out_special,
                         uint8_t* out_must23, cudaStream_t stream);
 
+/*
+ * Continuous-batching server.  Requests are device-resident buffers submitted
+ * from any thread; each is validated exactly as utf8_validate would, but many
+ * requests share one launch (a segment batch: each buffer checked on its
+ * own, the batch's tiles split evenly across the GPU).  A request is admitted
+ * while the bytes of admitted, unfinished requests stay within budget_bytes;
+ * later ones wait in arrival order.  A batch is launched when its oldest
+ * request has waited window_min_us and no batch is on the GPU, or has waited
+ * window_max_us, or max_batch requests are ready; up to `streams` batches run
+ * at once, so requests arriving while others are on the GPU are batched and
+ * launched without waiting for them.  The buffer of a request must stay
+ * valid until its result has been taken.
+ */
+typedef struct utf8_server utf8_server;
+
+typedef struct {
+    uint64_t budget_bytes;  /* default 8 GiB */
+    uint32_t window_min_us; /* default 50 */
+    uint32_t window_max_us; /* default 500 */
+    uint32_t max_batch;     /* requests per launch, default 4096 */
+    uint32_t streams;       /* batches in flight, default 4 (max 64) */
+} utf8_server_config;
+
+typedef struct {
+    uint64_t submitted, completed, batches, bytes, max_admitted_bytes, max_batch_seen;
+} utf8_server_stats;
+
+void utf8_server_default_config(utf8_server_config* cfg);
+
+/* NULL on error (utf8_last_error: UTF8_ERR_INVALID_ARG or UTF8_ERR_CUDA).
+ * Uses the current device; allocates its streams and descriptor buffers. */
+utf8_server* utf8_server_create(const utf8_server_config* cfg);
+
+/* Queues data[0 .. len) (device memory); *ticket identifies the request.
+ * UTF8_ERR_BUDGET if len alone exceeds the budget. */
+int utf8_server_submit(utf8_server* s, const uint8_t* data, size_t len, uint64_t* ticket);
+
+/* Waits up to timeout_us (< 0: forever) for a request; *valid = 1/0 and
+ * *latency_ns = time from arrival to result.  UTF8_ERR_TIMEOUT if not done. */
+int utf8_server_result(utf8_server* s, uint64_t ticket, int64_t timeout_us, int* valid,
+                       int64_t* latency_ns);
+
+/* Load replay (benchmarks and tests): submits request i (host arrays of
+ * device pointers and lengths) arrival_ns[i] after the call starts (busy
+ * wait), then waits for all; latency counts from the scheduled arrival. */
+int utf8_server_replay(utf8_server* s, const uint8_t* const* datas, const size_t* lens,
+                       const int64_t* arrival_ns, int64_t count, uint8_t* out_valid,
+                       int64_t* out_latency_ns);
+
+int utf8_server_stats_get(utf8_server* s, utf8_server_stats* out);
+
+/* Finishes all submitted requests, then frees the server. */
+void utf8_server_destroy(utf8_server* s);
+
 /* Status of the calling thread's last utf8_* call. */
 int utf8_last_error(void);
 

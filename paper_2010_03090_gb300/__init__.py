@@ -26,6 +26,26 @@ from ._lib import (  # noqa: F401
     utf8_validate_host_noalloc,
 )
 
+from .serve import Server  # noqa: E402,F401
+
+
+def _server_fn(name):
+    def call(*args):
+        from .serve import _bind
+        return getattr(_bind(), name)(*args)
+    call.__name__ = name
+    call.__doc__ = f"Direct C-ABI call {name}; see include/utf8gpu.h and serve.Server."
+    return call
+
+
+utf8_server_default_config = _server_fn("utf8_server_default_config")
+utf8_server_create = _server_fn("utf8_server_create")
+utf8_server_submit = _server_fn("utf8_server_submit")
+utf8_server_result = _server_fn("utf8_server_result")
+utf8_server_replay = _server_fn("utf8_server_replay")
+utf8_server_stats_get = _server_fn("utf8_server_stats_get")
+utf8_server_destroy = _server_fn("utf8_server_destroy")
+
 UTF8_OK = 0
 UTF8_ERR_INVALID_ARG = 1
 UTF8_ERR_CUDA = 2

@@ -14,7 +14,9 @@ EXPORTS = (
     "utf8_validate", "utf8_validate_async", "utf8_validate_batch", "utf8_validate_host",
     "utf8_classify_debug", "utf8_last_error", "utf8_error_string", "utf8_autotune",
     "utf8_tune_cache_load", "utf8_tune_cache_save", "utf8_config_json",
-    "utf8_validate_host_noalloc",
+    "utf8_validate_host_noalloc", "utf8_server_default_config", "utf8_server_create",
+    "utf8_server_submit", "utf8_server_result", "utf8_server_replay", "utf8_server_stats_get",
+    "utf8_server_destroy",
 )
 
 

@@ -29,6 +29,19 @@ uint64_t tile_bytes(const LaunchCfg& cfg);
 cudaError_t launch_classify_debug(const uint8_t* data, uint64_t n, uint8_t* out_special,
                                   uint8_t* out_must23, cudaStream_t st);
 
+// One independent buffer of a segment batch (segments.cu).
+struct SegmentDesc {
+  const uint8_t* data;
+  uint64_t len;
+};
+
+uint64_t segment_tiles(const uint8_t* data, uint64_t len, const LaunchCfg& cfg);
+
+// tile_prefix: device int64[count + 1], exclusive prefix of segment_tiles.
+cudaError_t launch_segments(const SegmentDesc* segs, const int64_t* tile_prefix, int64_t count,
+                            uint64_t total_tiles, uint8_t* out_valid, const LaunchCfg& cfg,
+                            int sm_count, cudaStream_t st);
+
 cudaError_t launch_batch(const uint8_t* data, const int64_t* offsets, int64_t count,
                          uint8_t* out_valid, const LaunchCfg& cfg, int sm_count, cudaStream_t st);
 

@@ -355,3 +355,24 @@ def serving_requests(seed: int = SEED_BASE + 4000, duration_s: float = 10.0,
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
     sizes = np.exp(rng.uniform(math.log(lo), math.log(hi), n)).astype(np.int64)
     return arrivals, sizes
+
+
+def serving_pool(count: int = 2048, lo: int = 64, hi: int = 16 << 20,
+                 invalid_fraction: float = 0.005, seed: int = SEED_BASE + 4000,
+                 threads: int | None = None):
+    """Request payloads for a serving run: ``count`` strings with log-uniform
+    sizes in [lo, hi], mixed content, a seeded fraction corrupted.  Requests
+    draw payloads uniformly, so their sizes are log-uniform too.  Returns
+    (data, offsets, indices of the corrupted payloads)."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(math.log(lo), math.log(hi), count)).astype(np.int64)
+    offsets = offsets_of(sizes)
+    data = fill_strings(offsets, UNIFORM, seed, threads)
+    bad = corrupt_strings(data, offsets, invalid_fraction, seed + 1)
+    return data, offsets, bad
+
+
+def poisson_arrivals_ns(count: int, rate: float, seed: int) -> np.ndarray:
+    """Arrival offsets (ns from the start) of a Poisson process."""
+    rng = np.random.default_rng(seed)
+    return (np.cumsum(rng.exponential(1.0 / rate, count)) * 1e9).astype(np.int64)
