@@ -53,10 +53,14 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--buffer-bytes", type=int, default=GIB)
     ap.add_argument("--no-extras", action="store_true", help="skip batch/serving extras")
+    ap.add_argument("--legs", default="main,e2e,cpu,batch,serve",
+                    help="comma-separated legs to run (profiling runs pick one)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-memory leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--variants", default="ascii,latin,cjk,emoji,uniform",
                     help="comma-separated subset of the content variants (profiling)")
+    ap.add_argument("--per-string-sample", type=int, default=20000,
+                    help="strings launched one by one for the per-string comparison")
     ap.add_argument("--serve-seconds", type=float, default=5.0,
                     help="length of the serving replay (Poisson arrivals at 50k req/s)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -255,6 +259,26 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     import torch
     import paper_2010_03090_gb300 as u
 
+    legs = set(args.legs.split(","))
+    if args.no_e2e:
+        legs.discard("e2e")
+    if args.no_cpu:
+        legs.discard("cpu")
+    if args.no_extras:
+        legs -= {"batch", "serve"}
+    if "main" not in legs:  # a single secondary leg (profiling runs)
+        torch.cuda.set_device(local_rank)
+        u.lib()
+        out = {}
+        if "batch" in legs:
+            out["batched_1m"] = bench_batch(u, torch, torch.cuda.Stream(),
+                                            float(measured_peaks().get("hbm_gbs") or FALLBACK_HBM_GBS),
+                                            args.per_string_sample)
+        if "serve" in legs:
+            out["serving"] = bench_serving(torch, args.serve_seconds)
+        print(json.dumps(out), flush=True)
+        return
+
     torch.cuda.set_device(local_rank)
     dist = None
     if world > 1:
@@ -324,7 +348,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     cfg = json.loads(u.utf8_config_json())
 
     # end to end: host buffers through the public host-memory entry point
-    e2e_steps = 0 if args.no_e2e else max(2, min(args.steps, 5))
+    e2e_steps = 1 if "e2e" in legs else 0
     e2e_value, e2e_flags = None, flags
     if e2e_steps:
         pinned = []
@@ -367,20 +391,22 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "gpu_launches": len(dev) * args.steps,
         "clocks": clock_info,
     }
-    if world == 1 and not args.no_cpu:
+    if world == 1 and "cpu" in legs:
         line["cpu_baseline"] = oracle_baseline(host, names, args.cpu_seconds)
-    if not args.no_extras and world == 1:
+    if world == 1 and legs & {"batch", "serve"}:
         del dev
         torch.cuda.empty_cache()
-        line["batched_1m"] = bench_batch(u, torch, stream, peak)
-        line["serving"] = bench_serving(torch, args.serve_seconds)
+        if "batch" in legs:
+            line["batched_1m"] = bench_batch(u, torch, stream, peak, args.per_string_sample)
+        if "serve" in legs:
+            line["serving"] = bench_serving(torch, args.serve_seconds)
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
 
 
-def bench_batch(u, torch, stream, peak: float) -> dict:
+def bench_batch(u, torch, stream, peak: float, sample: int = 20000) -> dict:
     """1M strings in one batch vs one launch per string (a sample)."""
     import synth
     data, offsets, _ = synth.workload_batch_1m()
@@ -401,7 +427,6 @@ def bench_batch(u, torch, stream, peak: float) -> dict:
     batch_gbs = data.size / (ms / 1e3) / 1e9
     moved = data.size + offsets.nbytes + (offsets.size - 1)
     # per-string launches on a sample of consecutive strings
-    sample = 20000
     one = torch.empty(1, dtype=torch.uint8, device="cuda")
     views = [d[offsets[i]:offsets[i + 1]] for i in range(sample)]
     with torch.cuda.stream(stream):
