@@ -176,10 +176,11 @@ def kernel_traffic(kernel: str):
     return rec
 
 
-def source_hash() -> str:
+def source_hash(files=("lookup.cuh", "tiles.cuh", "validate.cu")) -> str:
+    """Hash of the sources that make up validate_kernel."""
     csrc = os.path.join(ROOT, "paper_2010_03090_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(csrc)):
+    for name in files:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]

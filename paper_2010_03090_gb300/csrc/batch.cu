@@ -82,8 +82,14 @@ __global__ void __launch_bounds__(kBlockThreads)
 
   // absolute offset of virtual position 0 of the region
   const int64_t vbase = o_first - (int64_t)region.off;
-  // next boundary to handle: the first j with offsets[j] >= start of tile t0
-  int64_t bi = warp_lower_bound(offsets, 0, count + 1, vbase + (int64_t)(t0 * kTileBytes));
+  const int64_t range_lo = vbase + (int64_t)(t0 * kTileBytes);
+  const int64_t range_hi = vbase + (int64_t)(t1 * kTileBytes);
+  // boundaries of this warp: offsets[j] in [range_lo, range_hi), j in [b0, b1)
+  const int64_t b0 = warp_lower_bound(offsets, 0, count + 1, range_lo);
+  const int64_t b1 = warp_lower_bound(offsets, b0, count + 1, range_hi);
+  // strings that can hold a position of this warp: b0 - 1 .. b1 - 1
+  const int64_t own_lo = b0 > 0 ? b0 - 1 : 0;
+  const int64_t own_hi = b1 < count ? b1 : count;
 
   const uint32_t merge_sel = carry_merge_selector(lane);
   Carry carry = ascii_carry();
@@ -91,6 +97,9 @@ __global__ void __launch_bounds__(kBlockThreads)
   uint64_t in0, in1;
   interior_tiles<ROWS>(region, in0, in1);
   const uint8_t* lane_ptr = region.abase + t0 * kTileBytes + lane * 16;
+  int64_t next_group = b0;  // first boundary not yet checked
+  int64_t group_last = (next_group + kLanes < b1 ? next_group + kLanes : b1) - 1;
+  int64_t group_last_off = next_group < b1 ? offsets[group_last] : 0;
 
   for (uint64_t t = t0; t < t1; ++t, lane_ptr += kTileBytes) {
     const int64_t tile_lo = vbase + (int64_t)(t * kTileBytes);
@@ -108,34 +117,8 @@ __global__ void __launch_bounds__(kBlockThreads)
 #pragma unroll
       for (int m = 0; m < 8; ++m) any_err |= e[p][m];
 
-    // ---- boundaries inside this tile: exact head and tail checks ---------
-    const int64_t bi_tile = bi;
-    for (;;) {
-      const int64_t j = bi + lane;
-      const int64_t oj = j <= count ? offsets[j] : INT64_MAX;
-      const bool in = oj < tile_hi;
-      if (in) {
-        if (j >= 1) {  // tail of string j-1, which ends at oj
-          const int64_t s = offsets[j - 1];
-          const WordLut last = lut_word(gather4(data, oj - 4, s, oj));
-          if (word_error(last, ascii_lut()) != 0) out_valid[j - 1] = 0;
-        }
-        if (j < count) {  // head of string j, which starts at oj
-          const int64_t end = offsets[j + 1];
-          const WordLut first = lut_word(gather4(data, oj, oj, end));
-          if (word_error(ascii_lut(), first) != 0) out_valid[j] = 0;
-        }
-      }
-      const int n_in = __popc(__ballot_sync(kFull, in));
-      bi += n_in;
-      if (n_in < kLanes) break;
-    }
-
     // ---- charge streamed errors to strings (only where errors exist) -----
     if (__any_sync(kFull, any_err != 0)) {
-      // strings overlapping the tile: indices bi_tile - 1 .. bi - 1
-      const int64_t lo = bi_tile > 0 ? bi_tile - 1 : 0;
-      const int64_t hi = bi < count ? bi : count;  // owners are < count
 #pragma unroll
       for (int pr = 0; pr < ROWS / 2; ++pr) {
 #pragma unroll
@@ -145,12 +128,37 @@ __global__ void __launch_bounds__(kBlockThreads)
             const int byte = (__ffs(bits) - 1) >> 3;
             bits &= ~(0xFFu << (8 * byte));
             const int64_t p = tile_lo + (int64_t)interleaved_position<ROWS>(pr, m, byte, lane);
-            const int64_t own = last_at_most(offsets, lo, hi + 1, p);
+            const int64_t own = last_at_most(offsets, own_lo, own_hi + 1, p);
             if (own >= 0 && own < count && p - offsets[own] >= 3 && p < offsets[own + 1])
               out_valid[own] = 0;
           }
         }
       }
+    }
+
+    // ---- boundaries: exact head and tail checks, 32 at a time ------------
+    // A group is checked once the stream has passed its last boundary (its
+    // bytes are then recent in L2), or at the end of the warp's range.
+    while (next_group < b1) {
+      const int64_t last = group_last;
+      if (t + 1 < t1 && group_last_off >= tile_hi) break;
+      const int64_t j = next_group + lane;
+      if (j <= last) {
+        const int64_t oj = offsets[j];
+        if (j >= 1) {  // tail of string j-1, which ends at oj
+          const int64_t s = offsets[j - 1];
+          const WordLut tail = lut_word(gather4(data, oj - 4, s, oj));
+          if (word_error(tail, ascii_lut()) != 0) out_valid[j - 1] = 0;
+        }
+        if (j < count) {  // head of string j, which starts at oj
+          const int64_t end = offsets[j + 1];
+          const WordLut head = lut_word(gather4(data, oj, oj, end));
+          if (word_error(ascii_lut(), head) != 0) out_valid[j] = 0;
+        }
+      }
+      next_group = last + 1;
+      group_last = (next_group + kLanes < b1 ? next_group + kLanes : b1) - 1;
+      if (next_group < b1) group_last_off = offsets[group_last];
     }
   }
 }
