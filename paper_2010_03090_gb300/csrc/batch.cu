@@ -100,6 +100,8 @@ __global__ void __launch_bounds__(kBlockThreads)
   int64_t next_group = b0;  // first boundary not yet checked
   int64_t group_last = (next_group + kLanes < b1 ? next_group + kLanes : b1) - 1;
   int64_t group_last_off = next_group < b1 ? offsets[group_last] : 0;
+  uint4 next[ROWS];  // the next tile's loads, issued one tile ahead
+  load_tile<ROWS>(region, t0, in0, in1, lane, lane_ptr, next);
 
   for (uint64_t t = t0; t < t1; ++t, lane_ptr += kTileBytes) {
     const int64_t tile_lo = vbase + (int64_t)(t * kTileBytes);
@@ -107,8 +109,9 @@ __global__ void __launch_bounds__(kBlockThreads)
 
     // ---- stream the tile (plain `lookup` over the concatenation) ----------
     uint4 d[ROWS];
-    if (t >= in0 && t < in1) load_tile_interior<ROWS>(lane_ptr, d);
-    else load_tile_checked<ROWS>(region, t, lane, d);
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) d[r] = next[r];
+    if (t + 1 < t1) load_tile<ROWS>(region, t + 1, in0, in1, lane, lane_ptr + kTileBytes, next);
     uint32_t e[ROWS / 2][8];
     check_tile<ROWS>(d, carry, lane, merge_sel, e);
     uint32_t any_err = 0;

@@ -145,6 +145,14 @@ __device__ __forceinline__ void load_tile_interior(const uint8_t* lane_ptr, uint
   for (int r = 0; r < ROWS; ++r) d[r] = ld_stream(lane_ptr + r * kLanes * 16);
 }
 
+// Tile t, unchecked when it is interior (in0 <= t < in1), checked otherwise.
+template <int ROWS>
+__device__ __forceinline__ void load_tile(const Span& s, uint64_t t, uint64_t in0, uint64_t in1,
+                                          int lane, const uint8_t* lane_ptr, uint4 (&d)[ROWS]) {
+  if (t >= in0 && t < in1) load_tile_interior<ROWS>(lane_ptr, d);
+  else load_tile_checked<ROWS>(s, t, lane, d);
+}
+
 // Interior tiles of a stream: [first, last) (every granule inside [off, off + n)).
 template <int ROWS>
 __device__ __forceinline__ void interior_tiles(const Span& s, uint64_t& first, uint64_t& last) {
@@ -235,10 +243,15 @@ __device__ __forceinline__ uint32_t warp_check_tiles(const Span& s, uint64_t t_b
   uint64_t in0, in1;
   interior_tiles<ROWS>(s, in0, in1);
   const uint8_t* lane_ptr = s.abase + t_begin * tb + lane * 16;
+  // The next tile's loads are issued before the current tile is classified,
+  // so its memory latency overlaps the ALU-bound classification.
+  uint4 next[ROWS];
+  if (t_begin < t_end) load_tile<ROWS>(s, t_begin, in0, in1, lane, lane_ptr, next);
   for (uint64_t t = t_begin; t < t_end; ++t, lane_ptr += tb) {
     uint4 d[ROWS];
-    if (t >= in0 && t < in1) load_tile_interior<ROWS>(lane_ptr, d);
-    else load_tile_checked<ROWS>(s, t, lane, d);
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) d[r] = next[r];
+    if (t + 1 < t_end) load_tile<ROWS>(s, t + 1, in0, in1, lane, lane_ptr + tb, next);
     uint32_t e[ROWS / 2][8];
     check_tile<ROWS>(d, carry, lane, merge_sel, e);
 #pragma unroll
