@@ -184,16 +184,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_traffic(kernel: str):
+def kernel_traffic(kernel: str, rows: int):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (same hash); None otherwise."""
+    on the current kernel sources (same hash) and tile height; None otherwise."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f).get(kernel)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("source_hash") != source_hash():
+    if not rec or rec.get("source_hash") != source_hash() or rec.get("rows") != rows:
         return None
     return rec
 
@@ -373,7 +373,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         cls_gbs = cls_bytes / cls_s / 1e9
     else:
         alu_achieved, cls_gbs = None, None
-    traffic = kernel_traffic("validate_kernel")
+    traffic = kernel_traffic("validate_kernel", int(json.loads(u.utf8_config_json())["rows"]))
     per_variant = {nm: round(host[i].size / (per_buf_ms[:, i].mean() / 1e3) / 1e9, 1)
                    for i, nm in enumerate(names)}
     cfg = json.loads(u.utf8_config_json())

@@ -9,7 +9,7 @@ constexpr int kBlockThreads = 256;
 
 // Launch configuration (picked by the autotuner, or the defaults below).
 struct LaunchCfg {
-  int rows = 4;           // tile rows per warp (tile = rows * 512 bytes): 2, 4 or 8
+  int rows = 8;           // tile rows per warp (tile = rows * 512 bytes): 2, 4 or 8
   int blocks_per_sm = 8;  // resident CTAs per SM in the persistent grid
   int batch_rows = 4;     // tile rows for the batch kernel
   int batch_blocks_per_sm = 8;

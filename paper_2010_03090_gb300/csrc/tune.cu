@@ -110,7 +110,7 @@ LaunchCfg tuned_config(const char* gpu_name, int sm_count) {
 }
 
 void clamp_to_occupancy(LaunchCfg& cfg) {
-  if (cfg.rows != 2 && cfg.rows != 4 && cfg.rows != 8) cfg.rows = 4;
+  if (cfg.rows != 2 && cfg.rows != 4 && cfg.rows != 8) cfg.rows = 8;
   if (cfg.batch_rows != 2 && cfg.batch_rows != 4) cfg.batch_rows = 4;
   const int v = validate_blocks_per_sm(cfg.rows);
   const int b = batch_blocks_per_sm(cfg.batch_rows);
