@@ -59,7 +59,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--buffer-bytes", type=int, default=GIB)
     ap.add_argument("--no-extras", action="store_true", help="skip batch/serving extras")
-    ap.add_argument("--legs", default="main,e2e,cpu,batch,serve",
+    ap.add_argument("--legs", default="main,e2e,cpu,batch,serve,stream",
                     help="comma-separated legs to run (profiling runs pick one)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-memory leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
@@ -288,7 +288,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if args.no_cpu:
         legs.discard("cpu")
     if args.no_extras:
-        legs -= {"batch", "serve"}
+        legs -= {"batch", "serve", "stream"}
     if "main" not in legs:  # a single secondary leg (profiling runs)
         torch.cuda.set_device(local_rank)
         u.lib()
@@ -299,6 +299,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                                             args.per_string_sample)
         if "serve" in legs:
             out["serving"] = bench_serving(torch, args.serve_seconds)
+        if "stream" in legs:
+            out["streaming"] = bench_stream(u, torch)
         print(json.dumps(out), flush=True)
         return
 
@@ -439,13 +441,15 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     }
     if world == 1 and "cpu" in legs:
         line["cpu_baseline"] = oracle_baseline(host, names, args.cpu_seconds)
-    if world == 1 and legs & {"batch", "serve"}:
+    if world == 1 and legs & {"batch", "serve", "stream"}:
         del dev
         torch.cuda.empty_cache()
         if "batch" in legs:
             line["batched_1m"] = bench_batch(u, torch, stream, peak, args.per_string_sample)
         if "serve" in legs:
             line["serving"] = bench_serving(torch, args.serve_seconds)
+        if "stream" in legs:
+            line["streaming"] = bench_stream(u, torch)
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -491,6 +495,49 @@ def bench_batch(u, torch, stream, peak: float, sample: int = 20000) -> dict:
             "per_string_launch_gbs": round(per_gbs, 3),
             "per_string_launch_sample": sample,
             "speedup_vs_per_string": round(batch_gbs / per_gbs, 1)}
+
+
+def bench_stream(u, torch) -> dict:
+    """Chunked validation through the device-resident stream state: one 1 GiB
+    CJK-like buffer fed as consecutive chunks, against one call on the whole."""
+    import synth
+    buf = synth.fill_variant(1 << 30, "cjk", synth.SEED_BASE + 5000)
+    d = torch.from_numpy(buf).cuda()
+    out = torch.zeros(1, dtype=torch.uint8, device="cuda")
+    h = u.utf8_stream_create()
+    res = {}
+    try:
+        for chunk in (1 << 20, 16 << 20, 64 << 20):
+            views = [d[i:i + chunk] for i in range(0, d.numel(), chunk)]
+
+            def run():
+                u.utf8_stream_reset(h)
+                for v in views:
+                    u.utf8_stream_update(h, v)
+                u.utf8_stream_finish(h, out)
+            run()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 5
+            a.record()
+            for _ in range(reps):
+                run()
+            b.record()
+            torch.cuda.synchronize()
+            res[f"chunk_{chunk >> 20}MiB_gbs"] = round(d.numel() * reps / (a.elapsed_time(b) / 1e3) / 1e9, 1)
+            res[f"chunk_{chunk >> 20}MiB_valid"] = int(out.item())
+    finally:
+        u.utf8_stream_destroy(h)
+    one = torch.zeros(1, dtype=torch.uint8, device="cuda")
+    u.utf8_validate_async(d, one)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(5):
+        u.utf8_validate_async(d, one)
+    b.record()
+    torch.cuda.synchronize()
+    res["whole_buffer_gbs"] = round(d.numel() * 5 / (a.elapsed_time(b) / 1e3) / 1e9, 1)
+    return res
 
 
 def bench_serving(torch, seconds: float) -> dict:

@@ -97,6 +97,38 @@ int utf8_validate_batch(const uint8_t* data, const int64_t* offsets, int64_t cou
 bool utf8_validate_host(const uint8_t* host_data, size_t len, cudaStream_t stream);
 
 /*
+ * One chunk of a longer stream (the paper's loop carries the previous block
+ * and checks the end of the stream once: Section 6, Section 6.3).  data[0 ..
+ * len) (device memory) is checked as it would be inside the whole stream:
+ * `prefix` holds the prefix_len (0..3) bytes that precede the chunk in the
+ * stream, the byte just before it in bits 0..7, the one before that in bits
+ * 8..15, then bits 16..23 (prefix_len = 0 at the start of a stream).  With
+ * final_chunk != 0 the end of the stream after this chunk is checked too
+ * (an empty final chunk checks only the end).  The result is AND-ed into the
+ * device byte *out_valid: it is cleared on an error and never set, so the
+ * caller sets it to 1 first and any number of chunks (also on other streams or
+ * other GPUs, e.g. shards of one buffer) may share it.  Asynchronous.
+ */
+int utf8_validate_chunk(const uint8_t* data, size_t len, uint32_t prefix, int prefix_len,
+                        int final_chunk, uint8_t* out_valid, cudaStream_t stream);
+
+/*
+ * Stream validation with the carried state on the device (no host sync
+ * between chunks): the last three bytes of the stream so far and the result.
+ * utf8_stream_create allocates it (NULL on error), reset starts a new stream,
+ * update validates the next chunk (device memory; asynchronous; chunks may be
+ * reused buffers, the state keeps what it needs), finish checks the end of the
+ * stream and writes the result (1 = valid) to the device byte *out_valid.
+ * Calls on one state must be ordered (same stream, or synchronised).
+ */
+typedef struct utf8_stream utf8_stream;
+utf8_stream* utf8_stream_create(void);
+int utf8_stream_reset(utf8_stream* s, cudaStream_t stream);
+int utf8_stream_update(utf8_stream* s, const uint8_t* chunk, size_t len, cudaStream_t stream);
+int utf8_stream_finish(utf8_stream* s, uint8_t* out_valid, cudaStream_t stream);
+void utf8_stream_destroy(utf8_stream* s);
+
+/*
  * utf8_validate_host without any allocation, for callers that cannot allocate
  * GPU memory when they validate: services whose GPU memory is reserved up
  * front by a pool or another framework, latency-critical paths where

@@ -24,6 +24,12 @@ from ._lib import (  # noqa: F401
     utf8_validate_batch,
     utf8_validate_host,
     utf8_validate_host_noalloc,
+    utf8_validate_chunk,
+    utf8_stream_create,
+    utf8_stream_reset,
+    utf8_stream_update,
+    utf8_stream_finish,
+    utf8_stream_destroy,
 )
 
 from .serve import Server  # noqa: E402,F401

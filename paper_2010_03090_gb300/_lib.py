@@ -16,7 +16,8 @@ EXPORTS = (
     "utf8_tune_cache_load", "utf8_tune_cache_save", "utf8_config_json",
     "utf8_validate_host_noalloc", "utf8_server_default_config", "utf8_server_create",
     "utf8_server_submit", "utf8_server_result", "utf8_server_replay", "utf8_server_stats_get",
-    "utf8_server_destroy",
+    "utf8_server_destroy", "utf8_validate_chunk", "utf8_stream_create", "utf8_stream_reset",
+    "utf8_stream_update", "utf8_stream_finish", "utf8_stream_destroy",
 )
 
 
@@ -63,6 +64,18 @@ def lib() -> ctypes.CDLL:
             L.utf8_config_json.restype = i32
             L.utf8_validate_host_noalloc.argtypes = [vp, sz, vp]
             L.utf8_validate_host_noalloc.restype = ctypes.c_bool
+            L.utf8_validate_chunk.argtypes = [vp, sz, ctypes.c_uint32, i32, i32, vp, vp]
+            L.utf8_validate_chunk.restype = i32
+            L.utf8_stream_create.argtypes = []
+            L.utf8_stream_create.restype = vp
+            L.utf8_stream_reset.argtypes = [vp, vp]
+            L.utf8_stream_reset.restype = i32
+            L.utf8_stream_update.argtypes = [vp, vp, sz, vp]
+            L.utf8_stream_update.restype = i32
+            L.utf8_stream_finish.argtypes = [vp, vp, vp]
+            L.utf8_stream_finish.restype = i32
+            L.utf8_stream_destroy.argtypes = [vp]
+            L.utf8_stream_destroy.restype = None
             _lib = L
     return _lib
 
@@ -174,6 +187,42 @@ def utf8_validate_host_noalloc(host, stream=None) -> bool:
     ok = lib().utf8_validate_host_noalloc(p or None, n, _stream(stream))
     _check(lib().utf8_last_error(), "utf8_validate_host_noalloc")
     return bool(ok)
+
+
+def utf8_validate_chunk(data, prefix: bytes, final: bool, out_valid, stream=None) -> None:
+    """Validates one chunk of a stream given the (up to 3) bytes before it;
+    clears the device byte out_valid on an error (asynchronous)."""
+    p, n = _dev(data, "uint8", "data")
+    q, _ = _dev(out_valid, "uint8", "out_valid")
+    pre = bytes(prefix)[-3:]
+    packed = int.from_bytes(pre[::-1], "little")  # byte just before the chunk in bits 0..7
+    _check(lib().utf8_validate_chunk(p or None, n, packed, len(pre), int(bool(final)), q,
+                                     _stream(stream)), "utf8_validate_chunk")
+
+
+def utf8_stream_create():
+    h = lib().utf8_stream_create()
+    if not h:
+        raise Utf8Error(lib().utf8_last_error(), "utf8_stream_create")
+    return h
+
+
+def utf8_stream_reset(h, stream=None) -> None:
+    _check(lib().utf8_stream_reset(h, _stream(stream)), "utf8_stream_reset")
+
+
+def utf8_stream_update(h, chunk, stream=None) -> None:
+    p, n = _dev(chunk, "uint8", "chunk")
+    _check(lib().utf8_stream_update(h, p or None, n, _stream(stream)), "utf8_stream_update")
+
+
+def utf8_stream_finish(h, out_valid, stream=None) -> None:
+    q, _ = _dev(out_valid, "uint8", "out_valid")
+    _check(lib().utf8_stream_finish(h, q, _stream(stream)), "utf8_stream_finish")
+
+
+def utf8_stream_destroy(h) -> None:
+    lib().utf8_stream_destroy(h)
 
 
 def utf8_classify_debug(data, stream=None):

@@ -42,6 +42,14 @@ cudaError_t launch_segments(const SegmentDesc* segs, const int64_t* tile_prefix,
                             uint64_t total_tiles, uint8_t* out_valid, const LaunchCfg& cfg,
                             int sm_count, cudaStream_t st);
 
+// One chunk of a longer stream (stream.cu): prefix = the up to three bytes
+// before it (natural order in bytes 1..3, b[-1] in byte 3) or, if prefix_dev
+// is set, read from device memory (b[-3], b[-2], b[-1]); tail_out, if set,
+// receives the stream's new last three bytes.
+cudaError_t launch_chunk(const uint8_t* data, uint64_t n, uint32_t prefix,
+                         const uint8_t* prefix_dev, int final_chunk, uint8_t* out_valid,
+                         uint8_t* tail_out, int sm_count, cudaStream_t st);
+
 cudaError_t launch_batch(const uint8_t* data, const int64_t* offsets, int64_t count,
                          uint8_t* out_valid, const LaunchCfg& cfg, int sm_count, cudaStream_t st);
 

@@ -1,0 +1,111 @@
+"""Chunked validation (GPU): a buffer cut into chunks at arbitrary points
+(including inside characters, empty chunks, chunks shorter than 3 bytes,
+any alignment) gives the same result as the whole buffer, through the
+stateless chunk call and through the device-resident stream state."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2010_03090_gb300 as u  # noqa: E402
+
+CLASS = np.frombuffer(bytes([0x41, 0x80, 0x90, 0xA0, 0xBF, 0xC1, 0xC3, 0xE0, 0xE9, 0xED, 0xF0,
+                             0xF4, 0xF5, 0x00]), np.uint8)
+
+
+def _cuts(n, rng):
+    k = int(rng.integers(0, 12))
+    pts = sorted(set([0, n] + [int(x) for x in rng.integers(0, n + 1, k)]))
+    if rng.random() < 0.3 and n > 2:  # force tiny chunks
+        a = int(rng.integers(0, n - 2))
+        pts = sorted(set(pts + [a, a + 1, a + 2]))
+    return pts
+
+
+def _buffers(rng):
+    out = []
+    for i in range(160):
+        n = int(rng.integers(0, 3000)) if i % 4 else int(rng.integers(0, 40))
+        if i % 3 == 0:
+            b = CLASS[rng.integers(0, CLASS.size, n)]
+        else:
+            b = synth.fill(n, synth.UNIFORM, seed=i)
+            if i % 3 == 1 and n:
+                synth.inject_any(b, synth.ERROR_CLASSES[i % 7], rng)
+        out.append(b)
+    big = synth.fill(5 << 20, synth.CJK, seed=5)
+    out.append(big)
+    bad = big.copy()
+    synth.inject(bad, "too_short", rng, at=(1 << 20) - 1)
+    out.append(bad)
+    return out
+
+
+def test_chunks_equal_whole_buffer():
+    rng = np.random.default_rng(3)
+    flag = torch.ones(1, dtype=torch.uint8, device="cuda")
+    pool = torch.zeros((6 << 20) + 64, dtype=torch.uint8, device="cuda")
+    for b in _buffers(rng):
+        want = oracle.valid(b)
+        pts = _cuts(b.size, rng)
+        flag.fill_(1)
+        for k in range(len(pts) - 1):
+            lo, hi = pts[k], pts[k + 1]
+            shift = int(rng.integers(0, 16))
+            pool[shift:shift + hi - lo] = torch.from_numpy(b[lo:hi].copy()).cuda()
+            u.utf8_validate_chunk(pool[shift:shift + hi - lo], bytes(b[max(0, lo - 3):lo]),
+                                  k == len(pts) - 2, flag)
+        if len(pts) == 1:  # empty buffer: only the final (empty) chunk
+            u.utf8_validate_chunk(pool[:0], b"", True, flag)
+        torch.cuda.synchronize()
+        assert flag.item() == want, (b.size, pts)
+
+
+def test_stream_state_equals_whole_buffer():
+    rng = np.random.default_rng(4)
+    h = u.utf8_stream_create()
+    out = torch.zeros(1, dtype=torch.uint8, device="cuda")
+    ring = torch.zeros((6 << 20) + 64, dtype=torch.uint8, device="cuda")  # one reused buffer
+    try:
+        for b in _buffers(rng):
+            u.utf8_stream_reset(h)
+            pts = _cuts(b.size, rng)
+            for k in range(len(pts) - 1):
+                lo, hi = pts[k], pts[k + 1]
+                shift = int(rng.integers(0, 16))
+                ring[shift:shift + hi - lo] = torch.from_numpy(b[lo:hi].copy()).cuda()
+                u.utf8_stream_update(h, ring[shift:shift + hi - lo])
+            u.utf8_stream_finish(h, out)
+            torch.cuda.synchronize()
+            assert out.item() == oracle.valid(b), (b.size, pts)
+    finally:
+        u.utf8_stream_destroy(h)
+
+
+def test_shards_share_one_flag():
+    """Shards of one buffer (each given the 3 bytes before it) validated on
+    separate streams into one shared flag."""
+    rng = np.random.default_rng(5)
+    base = synth.fill(32 << 20, synth.UNIFORM, seed=9)
+    for trial in range(4):
+        b = base.copy()
+        if trial:
+            synth.inject_any(b, synth.ERROR_CLASSES[trial], rng, at=int(rng.integers(0, b.size)))
+        d = torch.from_numpy(b).cuda()
+        cuts = np.linspace(0, b.size, 9).astype(int)
+        flag = torch.ones(1, dtype=torch.uint8, device="cuda")
+        streams = [torch.cuda.Stream() for _ in range(len(cuts) - 1)]
+        torch.cuda.synchronize()
+        for k, st in enumerate(streams):
+            lo, hi = int(cuts[k]), int(cuts[k + 1])
+            u.utf8_validate_chunk(d[lo:hi], bytes(b[max(0, lo - 3):lo]), k == len(streams) - 1,
+                                  flag, stream=st)
+        torch.cuda.synchronize()
+        assert flag.item() == oracle.valid(b)
