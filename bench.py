@@ -59,7 +59,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--buffer-bytes", type=int, default=GIB)
     ap.add_argument("--no-extras", action="store_true", help="skip batch/serving extras")
-    ap.add_argument("--legs", default="main,e2e,cpu,batch,serve,stream",
+    ap.add_argument("--legs", default="main,e2e,cpu,batch,serve,stream,copy",
                     help="comma-separated legs to run (profiling runs pick one)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-memory leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
@@ -288,7 +288,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if args.no_cpu:
         legs.discard("cpu")
     if args.no_extras:
-        legs -= {"batch", "serve", "stream"}
+        legs -= {"batch", "serve", "stream", "copy"}
     if "main" not in legs:  # a single secondary leg (profiling runs)
         torch.cuda.set_device(local_rank)
         u.lib()
@@ -301,6 +301,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             out["serving"] = bench_serving(torch, args.serve_seconds)
         if "stream" in legs:
             out["streaming"] = bench_stream(u, torch)
+        if "copy" in legs:
+            out["copy_validate"] = bench_copy(u, torch)
         print(json.dumps(out), flush=True)
         return
 
@@ -441,7 +443,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     }
     if world == 1 and "cpu" in legs:
         line["cpu_baseline"] = oracle_baseline(host, names, args.cpu_seconds)
-    if world == 1 and legs & {"batch", "serve", "stream"}:
+    if world == 1 and legs & {"batch", "serve", "stream", "copy"}:
         del dev
         torch.cuda.empty_cache()
         if "batch" in legs:
@@ -450,6 +452,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             line["serving"] = bench_serving(torch, args.serve_seconds)
         if "stream" in legs:
             line["streaming"] = bench_stream(u, torch)
+        if "copy" in legs:
+            line["copy_validate"] = bench_copy(u, torch)
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -538,6 +542,39 @@ def bench_stream(u, torch) -> dict:
     torch.cuda.synchronize()
     res["whole_buffer_gbs"] = round(d.numel() * 5 / (a.elapsed_time(b) / 1e3) / 1e9, 1)
     return res
+
+
+def bench_copy(u, torch) -> dict:
+    """Copy + validate of a 1 GiB CJK-like buffer: one fused pass against a
+    device copy followed by validation of the copy."""
+    import synth
+    buf = synth.fill_variant(1 << 30, "cjk", synth.SEED_BASE + 6000)
+    src = torch.from_numpy(buf).cuda()
+    dst = torch.empty_like(src)
+    out = torch.zeros(1, dtype=torch.uint8, device="cuda")
+    reps = 5
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return src.numel() * reps / (a.elapsed_time(b) / 1e3) / 1e9
+
+    fused = timed(lambda: u.utf8_copy_validate(dst, src, out))
+    ok = int(out.item()) == 1 and bool(torch.equal(dst, src))
+
+    def two_pass():
+        dst.copy_(src)
+        u.utf8_validate_async(dst, out)
+    separate = timed(two_pass)
+    return {"fused_gbs": round(fused, 1), "copy_then_validate_gbs": round(separate, 1),
+            "speedup": round(fused / separate, 2), "hbm_bytes_per_input_byte": 2,
+            "correct": ok}
 
 
 def bench_serving(torch, seconds: float) -> dict:

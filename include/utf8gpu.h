@@ -97,6 +97,17 @@ int utf8_validate_batch(const uint8_t* data, const int64_t* offsets, int64_t cou
 bool utf8_validate_host(const uint8_t* host_data, size_t len, cudaStream_t stream);
 
 /*
+ * Copies src[0 .. len) to dst and validates it in the same pass (the bytes
+ * are read from HBM once): the ingest step "copy into place, then validate"
+ * fused.  dst, src: device memory, not overlapping (UTF8_ERR_INVALID_ARG
+ * otherwise); *out_valid (device byte) = 1 if valid, 0 if not.  When dst and
+ * src differ in alignment modulo 16 the call copies first and validates the
+ * copy (two passes, still on the GPU).  Asynchronous.
+ */
+int utf8_copy_validate(uint8_t* dst, const uint8_t* src, size_t len, uint8_t* out_valid,
+                       cudaStream_t stream);
+
+/*
  * One chunk of a longer stream (the paper's loop carries the previous block
  * and checks the end of the stream once: Section 6, Section 6.3).  data[0 ..
  * len) (device memory) is checked as it would be inside the whole stream:

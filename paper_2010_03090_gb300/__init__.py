@@ -25,6 +25,7 @@ from ._lib import (  # noqa: F401
     utf8_validate_host,
     utf8_validate_host_noalloc,
     utf8_validate_chunk,
+    utf8_copy_validate,
     utf8_stream_create,
     utf8_stream_reset,
     utf8_stream_update,

@@ -17,7 +17,7 @@ EXPORTS = (
     "utf8_validate_host_noalloc", "utf8_server_default_config", "utf8_server_create",
     "utf8_server_submit", "utf8_server_result", "utf8_server_replay", "utf8_server_stats_get",
     "utf8_server_destroy", "utf8_validate_chunk", "utf8_stream_create", "utf8_stream_reset",
-    "utf8_stream_update", "utf8_stream_finish", "utf8_stream_destroy",
+    "utf8_stream_update", "utf8_stream_finish", "utf8_stream_destroy", "utf8_copy_validate",
 )
 
 
@@ -64,6 +64,8 @@ def lib() -> ctypes.CDLL:
             L.utf8_config_json.restype = i32
             L.utf8_validate_host_noalloc.argtypes = [vp, sz, vp]
             L.utf8_validate_host_noalloc.restype = ctypes.c_bool
+            L.utf8_copy_validate.argtypes = [vp, vp, sz, vp, vp]
+            L.utf8_copy_validate.restype = i32
             L.utf8_validate_chunk.argtypes = [vp, sz, ctypes.c_uint32, i32, i32, vp, vp]
             L.utf8_validate_chunk.restype = i32
             L.utf8_stream_create.argtypes = []
@@ -187,6 +189,22 @@ def utf8_validate_host_noalloc(host, stream=None) -> bool:
     ok = lib().utf8_validate_host_noalloc(p or None, n, _stream(stream))
     _check(lib().utf8_last_error(), "utf8_validate_host_noalloc")
     return bool(ok)
+
+
+def utf8_copy_validate(dst, src, out_valid=None, stream=None):
+    """Copies the uint8 CUDA tensor src into dst (same size) and validates it
+    in one pass; returns the 1-element result tensor (1 = valid)."""
+    import torch
+    d, n = _dev(dst, "uint8", "dst")
+    s, m = _dev(src, "uint8", "src")
+    if n < m:
+        raise ValueError("dst is smaller than src")
+    if out_valid is None:
+        out_valid = torch.empty(1, dtype=torch.uint8, device=src.device)
+    q, _ = _dev(out_valid, "uint8", "out_valid")
+    _check(lib().utf8_copy_validate(d or None, s or None, m, q, _stream(stream)),
+           "utf8_copy_validate")
+    return out_valid
 
 
 def utf8_validate_chunk(data, prefix: bytes, final: bool, out_valid, stream=None) -> None:

@@ -249,6 +249,20 @@ bool utf8_validate_host(const uint8_t* host_data, size_t len, cudaStream_t strea
   return d->h_results[slot] == 1;
 }
 
+int utf8_copy_validate(uint8_t* dst, const uint8_t* src, size_t len, uint8_t* out_valid,
+                       cudaStream_t stream) {
+  if (out_valid == nullptr || ((dst == nullptr || src == nullptr) && len > 0))
+    return set_status(UTF8_ERR_INVALID_ARG);
+  const uintptr_t d = reinterpret_cast<uintptr_t>(dst), s = reinterpret_cast<uintptr_t>(src);
+  if (len > 0 && d < s + len && s < d + len) return set_status(UTF8_ERR_INVALID_ARG);  // overlap
+  DeviceState* dev = device();
+  if (!dev) return UTF8_ERR_CUDA;
+  if (!is_device_memory(out_valid) || (len > 0 && (!is_device_memory(dst) || !is_device_memory(src))))
+    return set_status(UTF8_ERR_INVALID_ARG);
+  return cuda_status(
+      launch_copy_validate(dst, src, len, out_valid, dev->cfg, dev->sm_count, stream));
+}
+
 int utf8_classify_debug(const uint8_t* data, size_t len, uint8_t* out_special,
                         uint8_t* out_must23, cudaStream_t stream) {
   if (out_special == nullptr || out_must23 == nullptr || (data == nullptr && len > 0))

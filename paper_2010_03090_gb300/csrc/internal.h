@@ -50,6 +50,11 @@ cudaError_t launch_chunk(const uint8_t* data, uint64_t n, uint32_t prefix,
                          const uint8_t* prefix_dev, int final_chunk, uint8_t* out_valid,
                          uint8_t* tail_out, int sm_count, cudaStream_t st);
 
+// Copies src to dst while validating it (copy.cu); result byte set by the call.
+cudaError_t launch_copy_validate(uint8_t* dst, const uint8_t* src, uint64_t n, uint8_t* out_valid,
+                                 const LaunchCfg& cfg, int sm_count, cudaStream_t st);
+int copy_blocks_per_sm(int rows, int wanted);
+
 cudaError_t launch_batch(const uint8_t* data, const int64_t* offsets, int64_t count,
                          uint8_t* out_valid, const LaunchCfg& cfg, int sm_count, cudaStream_t st);
 
