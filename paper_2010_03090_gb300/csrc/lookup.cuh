@@ -14,8 +14,9 @@
 // (prev3, prev2) pair checks them against the tables):
 //
 //  * Nibble selectors.  prmt takes four 4-bit selectors packed in 16 bits.
-//    The high (or low) nibbles of two words are packed into one 32-bit
-//    selector (low half: first word, high half: second word).
+//    In the streaming kernels two rows of a tile are processed side by side
+//    (lut_interleaved): interleaving their bytes lets one shift and one mask
+//    pack the selectors of eight bytes.
 //  * 16 entries from an 8-byte prmt table.  A selector nibble with bit 3 set
 //    makes prmt replicate the sign bit of the selected byte.  With the
 //    complemented high nibble (15 - n) the eight non-ASCII leads 8..F index
@@ -26,14 +27,13 @@
 //    plain low nibble (entries 0..7, sign mode gives 0xFF for 8..F) AND-ed
 //    with a lookup through the complemented low nibble (entries 8..F, 0xFF for
 //    0..7) gives the table exactly.
-//  * The previous-byte lookups are computed on the current bytes, then shifted
-//    by one byte with a funnel shift (the paper's prev<1>), so each byte is
-//    looked up once.
+//  * The previous-byte lookups are computed on the current bytes, then moved
+//    to the next position by a funnel shift (the paper's prev<1>), so each
+//    byte is looked up once.
 //  * must_be_2_3: one more high-nibble lookup gives bit 6 = (byte >= 0xE0)
-//    and bit 5 = (byte >= 0xF0).  A funnel shift by 17 bits moves bit 6 of
-//    the byte two back onto bit 7, a shift by 26 bits moves bit 5 of the byte
-//    three back onto bit 7; their OR under 0x80808080 is the paper's
-//    (prev2 >= 0xE0) | (prev3 >= 0xF0) mask.
+//    and bit 5 = (byte >= 0xF0); shifts move bit 6 of the byte two back and
+//    bit 5 of the byte three back onto bit 7, and their OR under 0x80808080
+//    is the paper's (prev2 >= 0xE0) | (prev3 >= 0xF0) mask.
 //
 // Bit assignment: the one printed in Table 8 (TOO_SHORT 0x01, TOO_LONG 0x02,
 // OVERLONG_3 0x04, TOO_LARGE 0x08, SURROGATE 0x10, OVERLONG_2 0x20,
