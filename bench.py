@@ -199,12 +199,16 @@ def kernel_traffic(kernel: str, rows: int):
 
 
 def source_hash(files=("lookup.cuh", "tiles.cuh", "validate.cu")) -> str:
-    """Hash of the sources that make up validate_kernel."""
+    """Hash of the code (comments and whitespace removed) of validate_kernel."""
+    import re
     csrc = os.path.join(ROOT, "paper_2010_03090_gb300", "csrc")
     h = hashlib.sha256()
     for name in files:
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(name.encode() + f.read())
+        with open(os.path.join(csrc, name)) as f:
+            code = f.read()
+        code = re.sub(r"/\*.*?\*/", "", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", "", code)
+        h.update(name.encode() + re.sub(r"\s+", "", code).encode())
     return h.hexdigest()[:16]
 
 
