@@ -231,7 +231,35 @@ def oracle_baseline(bufs, names, seconds: float) -> dict:
     return {"value": round(total / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
             "sample": f"last {per >> 20} MiB (from a character start) of each of the "
                       f"{len(bufs)} buffers, {total / 1e9:.2f} GB, {dt:.1f} s, one thread",
-            "flags": dict(zip(names, got))}
+            "flags": dict(zip(names, got)),
+            "all_cores": oracle_all_cores(samples, names, got)}
+
+
+def split_at_char_starts(buf: np.ndarray, pieces: int) -> np.ndarray:
+    """Offsets cutting buf into `pieces` parts, each cut backed up to a byte
+    that is not a continuation.  A buffer is valid exactly when every part is:
+    no character straddles a cut before a non-continuation byte, and a cut
+    that lands on a continuation (four or more in a row) makes a part invalid
+    that the whole buffer is invalid for anyway."""
+    cuts = [0] + [char_start(buf, buf.size * k // pieces) for k in range(1, pieces)] + [buf.size]
+    return np.maximum.accumulate(np.asarray(cuts, np.int64))
+
+
+def oracle_all_cores(samples, names, single_flags) -> dict:
+    """The same samples through the oracle on every host core: each sample is
+    cut at character starts into 4 parts per thread and the parts are checked
+    by the oracle's threaded batch call."""
+    import oracle
+    threads = max(len(os.sched_getaffinity(0)), 1)
+    cuts = [split_at_char_starts(s, 4 * threads) for s in samples]
+    t = time.perf_counter()
+    got = [bool(oracle.valid_batch(s, c, threads=threads).all()) for s, c in zip(samples, cuts)]
+    dt = time.perf_counter() - t
+    total = sum(s.size for s in samples)
+    return {"value": round(total / dt / 1e9, 3), "unit": "GB/s", "cores": threads,
+            "kind": "oracle", "sample": f"the same {total / 1e9:.2f} GB, each buffer cut at "
+                                        f"character starts into {4 * threads} parts",
+            "flags_match_single_thread": got == list(single_flags)}
 
 
 # ---------------------------------------------------------------------------
