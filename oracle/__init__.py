@@ -10,6 +10,9 @@ Contents
 * ``valid`` / ``valid_batch`` — the oracle proper: the RFC 3629 predicate of
   the paper's Section 3 (Table 1, rules a-f) as a plain decode loop in C
   (``utf8_oracle.c``).
+* ``locate`` / ``locate_batch`` — where validity ends: the length of the
+  longest valid prefix and the Section 3 rule (a-f, numbered 1-6) that the
+  next character breaks (``RULES``), by a plain decode loop.
 * ``fsm_valid`` — the Section 5 finite-state validator, an independent pin.
 * ``lookup_aid`` — the Section 6 ``lookup`` steps written out plainly in
   numpy (Table 7 pattern sets -> three nibble tables, Fig. 1 classification,
@@ -75,6 +78,11 @@ def _load(mutant: int = 0) -> ctypes.CDLL:
         lib.oracle_valid_all.restype = None
         lib.oracle_class_disagreements.argtypes = [u8p, ctypes.c_int, ctypes.c_int]
         lib.oracle_class_disagreements.restype = ctypes.c_int64
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        lib.oracle_locate.argtypes = [u8p, ctypes.c_size_t, i32p]
+        lib.oracle_locate.restype = ctypes.c_int64
+        lib.oracle_locate_batch.argtypes = [u8p, i64p, ctypes.c_int64, i64p, i32p, ctypes.c_int]
+        lib.oracle_locate_batch.restype = None
         _libs[mutant] = lib
         return lib
 
@@ -144,3 +152,41 @@ def class_disagreements(reps, max_len: int, mutant: int = 0) -> int:
     """Decode oracle vs FSM over every class string up to ``max_len``."""
     r = _as_u8(reps)
     return int(_load(mutant).oracle_class_disagreements(_ptr(r), r.size, max_len))
+
+
+# Section 3's rules, numbered as the paper letters them (0: valid).
+RULES = {0: "valid", 1: "a: 5+ byte", 2: "b: too short", 3: "c: too long", 4: "d: overlong",
+         5: "e: too large", 6: "f: surrogate"}
+
+
+def locate(buf, mutant: int = 0) -> tuple[int, int]:
+    """(length of the longest valid prefix, rule 0-6 broken by the next
+    character); (len(buf), 0) for valid input."""
+    a = _as_u8(buf)
+    rule = ctypes.c_int32(-1)
+    if a.size == 0:
+        a = np.zeros(1, dtype=np.uint8)
+        pos = _load(mutant).oracle_locate(_ptr(a), 0, ctypes.byref(rule))
+    else:
+        pos = _load(mutant).oracle_locate(_ptr(a), a.size, ctypes.byref(rule))
+    return int(pos), int(rule.value)
+
+
+def locate_batch(data, offsets, threads: int = 1, mutant: int = 0):
+    """Per string k = data[offsets[k]:offsets[k+1]]: (positions relative to
+    the string's start as int64, rules as int32)."""
+    d = _as_u8(data)
+    o = np.ascontiguousarray(offsets, dtype=np.int64)
+    count = max(o.size - 1, 0)
+    pos = np.empty(count, dtype=np.int64)
+    rule = np.empty(count, dtype=np.int32)
+    if count == 0:
+        return pos, rule
+    if o[0] < 0 or o[-1] > d.size or np.any(np.diff(o) < 0):
+        raise ValueError("offsets must be non-decreasing and within the data")
+    if d.size == 0:
+        d = np.zeros(1, dtype=np.uint8)
+    _load(mutant).oracle_locate_batch(_ptr(d), _ptr(o, ctypes.c_int64), count,
+                                      _ptr(pos, ctypes.c_int64), _ptr(rule, ctypes.c_int32),
+                                      int(threads))
+    return pos, rule

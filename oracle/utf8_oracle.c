@@ -14,6 +14,10 @@
  * check and accumulate the continuation bytes, then range-check the decoded
  * code point.  It is branchy and slow on purpose.
  *
+ * oracle_locate extends the boolean with where it fails: the length of the
+ * longest valid prefix and the Section 3 rule (a-f) that the next character
+ * breaks, by the same kind of plain decode loop.
+ *
  * A second, independent validator, the finite-state machine of Section 5
  * (its state-transition table), lives here as well.  It is not the oracle;
  * the tests use it as one more pin on the oracle (exhaustive agreement on
@@ -250,4 +254,96 @@ int64_t oracle_class_disagreements(const uint8_t* reps, int nreps, int max_len)
         }
     }
     return bad;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Where validity ends (reported beside the paper's boolean).               */
+/*                                                                          */
+/* position: the length of the longest prefix of s that is valid under the */
+/* Section 3 predicate; it is n exactly when s is valid.  rule: which of    */
+/* the Section 3 rules the character starting at `position` breaks,         */
+/* numbered as the paper letters them: 1 = a (5+ byte: a lead with five or  */
+/* more header bits), 2 = b (too short: fewer continuation bytes than the   */
+/* lead announces, before another byte or the end), 3 = c (too long: a      */
+/* continuation byte where a character must start), 4 = d (overlong),       */
+/* 5 = e (too large), 6 = f (surrogate); 0 when s is valid.  The rules are  */
+/* checked in decoding order (header bits, then each continuation byte,     */
+/* then the decoded code point), and on a character whose continuation      */
+/* bytes are all present at most one of d, e and f can hold.                */
+/* ------------------------------------------------------------------------ */
+int64_t oracle_locate(const uint8_t* s, size_t n, int32_t* rule)
+{
+    size_t i = 0;
+    while (i < n) {
+        uint32_t lead = s[i];
+        uint32_t len, cp, min_cp;
+        if (lead < 0x80) {
+            i += 1;
+            continue;
+        }
+        if ((lead >> 6) == 0x2) { *rule = 3; return (int64_t)i; }      /* rule c */
+        if ((lead >> 5) == 0x6) {
+            len = 2; cp = lead & 0x1F; min_cp = 0x80;
+        } else if ((lead >> 4) == 0xE) {
+            len = 3; cp = lead & 0x0F; min_cp = 0x800;
+        } else if ((lead >> 3) == 0x1E) {
+            len = 4; cp = lead & 0x07; min_cp = 0x10000;
+        } else {
+            *rule = 1; return (int64_t)i;                              /* rule a */
+        }
+        for (uint32_t k = 1; k < len; ++k) {
+            if (i + k >= n || (s[i + k] >> 6) != 0x2) {
+                *rule = 2;                                             /* rule b */
+#if ORACLE_MUTANT == 7                      /* mutant: the missing byte's index */
+                return (int64_t)(i + k);
+#else
+                return (int64_t)i;
+#endif
+            }
+            cp = (cp << 6) | (s[i + k] & 0x3F);
+        }
+#if ORACLE_MUTANT == 8                      /* mutant: C0/C1 leads taken as rule a */
+        if (lead == 0xC0 || lead == 0xC1) { *rule = 1; return (int64_t)i; }
+#endif
+        if (cp < min_cp) { *rule = 4; return (int64_t)i; }             /* rule d */
+        if (cp > 0x10FFFF) { *rule = 5; return (int64_t)i; }           /* rule e */
+        if (cp >= 0xD800 && cp <= 0xDFFF) { *rule = 6; return (int64_t)i; }  /* f */
+        i += len;
+    }
+    *rule = 0;
+    return (int64_t)n;
+}
+
+/* Per string k of a batch: position relative to the string's start, rule. */
+typedef struct {
+    const uint8_t* data; const int64_t* offsets; int64_t lo, hi;
+    int64_t* pos; int32_t* rule;
+} locate_job;
+
+static void* locate_worker(void* arg)
+{
+    locate_job* j = (locate_job*)arg;
+    for (int64_t k = j->lo; k < j->hi; ++k)
+        j->pos[k] = oracle_locate(j->data + j->offsets[k],
+                                  (size_t)(j->offsets[k + 1] - j->offsets[k]), &j->rule[k]);
+    return NULL;
+}
+
+void oracle_locate_batch(const uint8_t* data, const int64_t* offsets, int64_t count,
+                         int64_t* pos, int32_t* rule, int threads)
+{
+    if (threads < 1) threads = 1;
+    if (threads > 256) threads = 256;
+    if (count < 2 * threads) threads = 1;
+    pthread_t tid[256];
+    locate_job job[256];
+    for (int t = 0; t < threads; ++t) {
+        job[t].data = data; job[t].offsets = offsets; job[t].pos = pos; job[t].rule = rule;
+        job[t].lo = count * t / threads;
+        job[t].hi = count * (t + 1) / threads;
+        if (threads > 1) pthread_create(&tid[t], NULL, locate_worker, &job[t]);
+        else locate_worker(&job[t]);
+    }
+    if (threads > 1)
+        for (int t = 0; t < threads; ++t) pthread_join(tid[t], NULL);
 }
