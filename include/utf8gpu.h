@@ -88,6 +88,69 @@ int utf8_validate_batch(const uint8_t* data, const int64_t* offsets, int64_t cou
                         uint8_t* out_valid, cudaStream_t stream);
 
 /*
+ * Where validation fails (the paper's validators answer valid / invalid;
+ * these report where and why, from the same `lookup` pass).
+ *
+ * position: the length of the longest prefix of the input that is valid
+ *   UTF-8; it equals the input's length exactly when the input is valid.
+ * rule: the Section 3 rule that the character starting at `position` breaks,
+ *   numbered as the paper letters the rules a-f (utf8_rule); UTF8_RULE_NONE
+ *   when the input is valid.  Rules are taken in decoding order: the lead's
+ *   header bits (a, c), then each continuation byte (b), then the decoded
+ *   code point (d, e, f; at most one of them can hold).
+ *
+ * How it is computed: the `lookup` classification (Section 6) marks the first
+ * erroneous position p, which lies 0..3 bytes after the failing character's
+ * start; the position is the last m <= p at which no character is cut (the
+ * end-of-stream check of Section 6.3 applied to the prefix), and the rule
+ * comes from decoding the at most four bytes at m.
+ */
+enum utf8_rule {
+    UTF8_RULE_NONE = 0,
+    UTF8_RULE_5PLUS_BYTE = 1, /* a: lead byte with five or more header bits (F8..FF) */
+    UTF8_RULE_TOO_SHORT = 2,  /* b: fewer continuation bytes than the lead announces */
+    UTF8_RULE_TOO_LONG = 3,   /* c: continuation byte where a character must start */
+    UTF8_RULE_OVERLONG = 4,   /* d: code point below the minimum for its length */
+    UTF8_RULE_TOO_LARGE = 5,  /* e: code point above U+10FFFF */
+    UTF8_RULE_SURROGATE = 6   /* f: code point in U+D800..U+DFFF */
+};
+
+typedef struct {
+    uint64_t position; /* length of the longest valid prefix */
+    int32_t rule;      /* enum utf8_rule */
+    int32_t reserved;  /* 0 */
+} utf8_error_info;
+
+/*
+ * Locates the first error of data[0 .. len) (device memory).  *out (device
+ * memory, 8-byte aligned, 16 bytes) receives the result when the stream
+ * reaches it; it is also the work area of the call, so nothing else may use
+ * it until then.  No allocation and no synchronisation (graph capturable).
+ * Asynchronous; returns a status (UTF8_ERR_INVALID_ARG for a null or host
+ * pointer or a misaligned out).
+ */
+int utf8_locate_error_async(const uint8_t* data, size_t len, utf8_error_info* out,
+                            cudaStream_t stream);
+
+/*
+ * Synchronous form: *out_host (host memory) receives the result.  Uses a
+ * library ring of device result slots; synchronises `stream`.
+ */
+int utf8_locate_error(const uint8_t* data, size_t len, utf8_error_info* out_host,
+                      cudaStream_t stream);
+
+/*
+ * Per string of a batch (the layout and rules of utf8_validate_batch): out is
+ * a device array of `count` utf8_error_info (8-byte aligned), position
+ * relative to the string's start.  All strings in one launch sequence: the
+ * batch pass marks each string's first erroneous position with an atomic
+ * minimum in out[i].position, then one thread per string settles position and
+ * rule.  Asynchronous; returns a status.
+ */
+int utf8_locate_errors_batch(const uint8_t* data, const int64_t* offsets, int64_t count,
+                             utf8_error_info* out, cudaStream_t stream);
+
+/*
  * Validates a buffer in HOST memory: copies it to the GPU through a
  * library-owned staging ring (pinned or pageable source; chunks of the copy
  * overlap with validation of earlier chunks, the 3 bytes before each chunk

@@ -31,6 +31,12 @@ from ._lib import (  # noqa: F401
     utf8_stream_update,
     utf8_stream_finish,
     utf8_stream_destroy,
+    utf8_locate_error,
+    utf8_locate_error_async,
+    utf8_locate_errors_batch,
+    error_info_fields,
+    ErrorInfo,
+    RULES,
 )
 
 from .serve import Server  # noqa: E402,F401

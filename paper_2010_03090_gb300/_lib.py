@@ -18,7 +18,18 @@ EXPORTS = (
     "utf8_server_submit", "utf8_server_result", "utf8_server_replay", "utf8_server_stats_get",
     "utf8_server_destroy", "utf8_validate_chunk", "utf8_stream_create", "utf8_stream_reset",
     "utf8_stream_update", "utf8_stream_finish", "utf8_stream_destroy", "utf8_copy_validate",
+    "utf8_locate_error", "utf8_locate_error_async", "utf8_locate_errors_batch",
 )
+
+# Section 3's rules a-f as the library numbers them (enum utf8_rule).
+RULES = {0: "valid", 1: "a: 5+ byte", 2: "b: too short", 3: "c: too long", 4: "d: overlong",
+         5: "e: too large", 6: "f: surrogate"}
+
+
+class ErrorInfo(ctypes.Structure):
+    """utf8_error_info: longest valid prefix and the rule the next character breaks."""
+    _fields_ = [("position", ctypes.c_uint64), ("rule", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class Utf8Error(RuntimeError):
@@ -78,6 +89,12 @@ def lib() -> ctypes.CDLL:
             L.utf8_stream_finish.restype = i32
             L.utf8_stream_destroy.argtypes = [vp]
             L.utf8_stream_destroy.restype = None
+            L.utf8_locate_error.argtypes = [vp, sz, ctypes.POINTER(ErrorInfo), vp]
+            L.utf8_locate_error.restype = i32
+            L.utf8_locate_error_async.argtypes = [vp, sz, vp, vp]
+            L.utf8_locate_error_async.restype = i32
+            L.utf8_locate_errors_batch.argtypes = [vp, vp, i64, vp, vp]
+            L.utf8_locate_errors_batch.restype = i32
             _lib = L
     return _lib
 
@@ -157,6 +174,60 @@ def utf8_validate_batch(data, offsets, out_valid=None, stream=None):
     _check(lib().utf8_validate_batch(p or None, q, count, r, _stream(stream)),
            "utf8_validate_batch")
     return out_valid
+
+
+def utf8_locate_error(data, stream=None) -> tuple[int, int]:
+    """(length of the longest valid prefix, rule 0-6) of a uint8 CUDA tensor;
+    synchronises the stream."""
+    p, n = _dev(data, "uint8", "data")
+    info = ErrorInfo()
+    _check(lib().utf8_locate_error(p or None, n, ctypes.byref(info), _stream(stream)),
+           "utf8_locate_error")
+    return int(info.position), int(info.rule)
+
+
+def utf8_locate_error_async(data, out=None, stream=None):
+    """Queues the error location of data into `out`, an int64 CUDA tensor of
+    two elements holding one utf8_error_info (see error_info_fields)."""
+    import torch
+    p, n = _dev(data, "uint8", "data")
+    if out is None:
+        out = torch.empty(2, dtype=torch.int64, device=data.device)
+    q, k = _dev(out, "int64", "out")
+    if k < 2:
+        raise ValueError("out needs two int64 elements")
+    _check(lib().utf8_locate_error_async(p or None, n, q, _stream(stream)),
+           "utf8_locate_error_async")
+    return out
+
+
+def utf8_locate_errors_batch(data, offsets, out=None, stream=None):
+    """Per string data[offsets[i]:offsets[i+1]]: one utf8_error_info, as an
+    int64 CUDA tensor of shape (count, 2) (asynchronous; see error_info_fields)."""
+    import torch
+    if isinstance(data, torch.Tensor) and data.numel() == 0:
+        data = torch.zeros(16, dtype=torch.uint8, device=offsets.device)  # any device byte
+    p, _ = _dev(data, "uint8", "data")
+    q, m = _dev(offsets, "int64", "offsets")
+    count = m - 1
+    if count < 0:
+        raise ValueError("offsets needs at least one entry")
+    if out is None:
+        out = torch.empty((max(count, 0), 2), dtype=torch.int64, device=offsets.device)
+    r, k = _dev(out, "int64", "out")
+    if k < 2 * count:
+        raise ValueError("out is too small")
+    _check(lib().utf8_locate_errors_batch(p or None, q, count, r, _stream(stream)),
+           "utf8_locate_errors_batch")
+    return out
+
+
+def error_info_fields(out):
+    """(positions int64, rules int32) views of utf8_error_info records held in
+    an int64 tensor of shape (..., 2)."""
+    import torch
+    t = out.reshape(-1, 2)
+    return t[:, 0], (t[:, 1] & 0xFFFFFFFF).to(torch.int32)  # rule: low half, little-endian
 
 
 def utf8_validate_host(host, stream=None) -> bool:

@@ -32,6 +32,7 @@ inline int set_status(int s) {
 
 constexpr int kMaxDevices = 64;
 constexpr uint32_t kResultSlots = 4096;
+constexpr uint32_t kInfoSlots = 1024;  // utf8_error_info slots of utf8_locate_error
 constexpr uint64_t kStageChunk = 64ull << 20;   // bytes per pipelined host copy
 constexpr uint64_t kStageWindow = 4ull << 30;   // largest staging buffer
 constexpr int kStageEvents = 64;
@@ -53,6 +54,9 @@ struct DeviceState {
   uint8_t* d_results = nullptr;  // kResultSlots result bytes
   uint8_t* h_results = nullptr;  // pinned mirror
   std::atomic<uint32_t> next_slot{0};
+  utf8_error_info* d_info = nullptr;  // kInfoSlots error locations
+  utf8_error_info* h_info = nullptr;  // pinned mirror
+  std::atomic<uint32_t> next_info{0};
   // host-memory path
   std::mutex stage_mu;
   uint8_t* d_stage = nullptr;
@@ -74,6 +78,9 @@ void init_device(DeviceState& d, int dev) {
     e = cudaMalloc(&d.d_results, kResultSlots);
   }
   if (e == cudaSuccess) e = cudaHostAlloc(&d.h_results, kResultSlots, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaMalloc(&d.d_info, kInfoSlots * sizeof(utf8_error_info));
+  if (e == cudaSuccess)
+    e = cudaHostAlloc(&d.h_info, kInfoSlots * sizeof(utf8_error_info), cudaHostAllocDefault);
   d.init_error = e;
 }
 
@@ -174,6 +181,55 @@ int utf8_validate_batch(const uint8_t* data, const int64_t* offsets, int64_t cou
   if (!is_device_memory(data) || !is_device_memory(offsets) || !is_device_memory(out_valid))
     return set_status(UTF8_ERR_INVALID_ARG);
   return cuda_status(launch_batch(data, offsets, count, out_valid, d->cfg, d->sm_count, stream));
+}
+
+int utf8_locate_error_async(const uint8_t* data, size_t len, utf8_error_info* out,
+                            cudaStream_t stream) {
+  if (out == nullptr || (data == nullptr && len > 0) ||
+      (reinterpret_cast<uintptr_t>(out) & 7) != 0)
+    return set_status(UTF8_ERR_INVALID_ARG);
+  DeviceState* d = device();
+  if (!d) return UTF8_ERR_CUDA;
+  if (!is_device_memory(out) || (len > 0 && !is_device_memory(data)))
+    return set_status(UTF8_ERR_INVALID_ARG);
+  return cuda_status(launch_locate(data, len, out, d->cfg, d->sm_count, stream));
+}
+
+int utf8_locate_error(const uint8_t* data, size_t len, utf8_error_info* out_host,
+                      cudaStream_t stream) {
+  if (out_host == nullptr || (data == nullptr && len > 0)) return set_status(UTF8_ERR_INVALID_ARG);
+  if (len == 0) {
+    out_host->position = 0;
+    out_host->rule = UTF8_RULE_NONE;
+    out_host->reserved = 0;
+    return set_status(UTF8_OK);
+  }
+  DeviceState* d = device();
+  if (!d) return UTF8_ERR_CUDA;
+  if (!is_device_memory(data)) return set_status(UTF8_ERR_INVALID_ARG);
+  const uint32_t slot = d->next_info.fetch_add(1) % kInfoSlots;
+  cudaError_t e = launch_locate(data, len, d->d_info + slot, d->cfg, d->sm_count, stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d->h_info + slot, d->d_info + slot, sizeof(utf8_error_info),
+                        cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  *out_host = d->h_info[slot];
+  return set_status(UTF8_OK);
+}
+
+int utf8_locate_errors_batch(const uint8_t* data, const int64_t* offsets, int64_t count,
+                             utf8_error_info* out, cudaStream_t stream) {
+  if (count < 0) return set_status(UTF8_ERR_INVALID_ARG);
+  if (count == 0) return set_status(UTF8_OK);
+  if (data == nullptr || offsets == nullptr || out == nullptr ||
+      (reinterpret_cast<uintptr_t>(out) & 7) != 0)
+    return set_status(UTF8_ERR_INVALID_ARG);
+  DeviceState* d = device();
+  if (!d) return UTF8_ERR_CUDA;
+  if (!is_device_memory(data) || !is_device_memory(offsets) || !is_device_memory(out))
+    return set_status(UTF8_ERR_INVALID_ARG);
+  return cuda_status(launch_locate_batch(data, offsets, count, out, d->cfg, d->sm_count, stream));
 }
 
 bool utf8_validate_host(const uint8_t* host_data, size_t len, cudaStream_t stream) {

@@ -22,11 +22,14 @@
 // p lies in that string's first three bytes (the head check decides those).
 // Boundary o_j is handled by the warp whose tile holds its position, so each
 // is handled once; flags only ever go from 1 (set before the launch) to 0.
+// With LOCATE the same checks lower each string's first erroneous position
+// (an atomic minimum, string-relative) instead of clearing its flag.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "internal.h"
 #include "tune.h"
+#include "locate.cuh"
 #include "lookup.cuh"
 #include "search.cuh"
 #include "tiles.cuh"
@@ -62,10 +65,22 @@ __device__ int64_t warp_lower_bound(const int64_t* offsets, int64_t lo, int64_t 
   return lb_final(lo, hi, __ballot_sync(kFull, ge));
 }
 
-template <int ROWS>
+// An error at `rel` bytes into string j: its flag is cleared, or (LOCATE) its
+// first erroneous position is lowered to rel (see locate.cuh).
+template <bool LOCATE>
+__device__ __forceinline__ void charge(uint8_t* out_valid, utf8_error_info* out_err, int64_t j,
+                                       int64_t rel) {
+  if constexpr (LOCATE) {
+    mark_first_error(&out_err[j], (uint64_t)rel);
+  } else {
+    out_valid[j] = 0;
+  }
+}
+
+template <int ROWS, bool LOCATE>
 __global__ void __launch_bounds__(kBlockThreads)
     batch_kernel(const uint8_t* __restrict__ data, const int64_t* __restrict__ offsets,
-                 int64_t count, uint8_t* __restrict__ out_valid) {
+                 int64_t count, uint8_t* __restrict__ out_valid, utf8_error_info* out_err) {
   constexpr uint64_t kTileBytes = (uint64_t)kLanes * ROWS * 16;
   // The region [offsets[0], offsets[count]) is read on the device, so the
   // launch needs nothing from the host but the pointers (graph capturable).
@@ -133,7 +148,7 @@ __global__ void __launch_bounds__(kBlockThreads)
             const int64_t p = tile_lo + (int64_t)interleaved_position<ROWS>(pr, m, byte, lane);
             const int64_t own = last_at_most(offsets, own_lo, own_hi + 1, p);
             if (own >= 0 && own < count && p - offsets[own] >= 3 && p < offsets[own + 1])
-              out_valid[own] = 0;
+              charge<LOCATE>(out_valid, out_err, own, p - offsets[own]);
           }
         }
       }
@@ -151,12 +166,14 @@ __global__ void __launch_bounds__(kBlockThreads)
         if (j >= 1) {  // tail of string j-1, which ends at oj
           const int64_t s = offsets[j - 1];
           const WordLut tail = lut_word(gather4(data, oj - 4, s, oj));
-          if (word_error(tail, ascii_lut()) != 0) out_valid[j - 1] = 0;
+          const uint32_t te = word_error(tail, ascii_lut());  // positions oj .. oj+3
+          if (te != 0) charge<LOCATE>(out_valid, out_err, j - 1, oj - s + ((__ffs(te) - 1) >> 3));
         }
         if (j < count) {  // head of string j, which starts at oj
           const int64_t end = offsets[j + 1];
           const WordLut head = lut_word(gather4(data, oj, oj, end));
-          if (word_error(ascii_lut(), head) != 0) out_valid[j] = 0;
+          const uint32_t he = word_error(ascii_lut(), head);  // positions oj .. oj+3
+          if (he != 0) charge<LOCATE>(out_valid, out_err, j, (__ffs(he) - 1) >> 3);
         }
       }
       next_group = last + 1;
@@ -166,12 +183,13 @@ __global__ void __launch_bounds__(kBlockThreads)
   }
 }
 
-template <int ROWS>
+template <int ROWS, bool LOCATE = false>
 static cudaError_t launch_batch_rows(const uint8_t* data, const int64_t* offsets, int64_t count,
                                      uint8_t* out_valid, int blocks_per_sm, int sm_count,
-                                     cudaStream_t st) {
+                                     cudaStream_t st, utf8_error_info* out_err = nullptr) {
   const unsigned grid = (unsigned)(sm_count * blocks_per_sm);
-  batch_kernel<ROWS><<<grid, kBlockThreads, 0, st>>>(data, offsets, count, out_valid);
+  batch_kernel<ROWS, LOCATE><<<grid, kBlockThreads, 0, st>>>(data, offsets, count, out_valid,
+                                                              out_err);
   return cudaGetLastError();
 }
 
@@ -188,6 +206,18 @@ cudaError_t launch_batch(const uint8_t* data, const int64_t* offsets, int64_t co
   }
 }
 
+cudaError_t launch_batch_first_errors(const uint8_t* data, const int64_t* offsets, int64_t count,
+                                      utf8_error_info* out, const LaunchCfg& cfg, int sm_count,
+                                      cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  switch (cfg.batch_rows) {
+    case 4: return launch_batch_rows<4, true>(data, offsets, count, nullptr,
+                                              cfg.batch_blocks_per_sm, sm_count, st, out);
+    default: return launch_batch_rows<2, true>(data, offsets, count, nullptr,
+                                               cfg.batch_blocks_per_sm, sm_count, st, out);
+  }
+}
+
 }  // namespace utf8gpu
 
 namespace utf8gpu {
@@ -196,8 +226,8 @@ int batch_blocks_per_sm(int rows) {
   int n = 0;
   cudaError_t e;
   switch (rows) {
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<4>, kBlockThreads, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<2>, kBlockThreads, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<4, false>, kBlockThreads, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<2, false>, kBlockThreads, 0); break;
   }
   if (e != cudaSuccess) { cudaGetLastError(); return 1; }
   return n > 0 ? n : 1;

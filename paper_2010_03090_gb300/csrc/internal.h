@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "utf8gpu.h"
+
 namespace utf8gpu {
 
 constexpr int kBlockThreads = 256;
@@ -57,5 +59,17 @@ int copy_blocks_per_sm(int rows, int wanted);
 
 cudaError_t launch_batch(const uint8_t* data, const int64_t* offsets, int64_t count,
                          uint8_t* out_valid, const LaunchCfg& cfg, int sm_count, cudaStream_t st);
+
+// Error location (locate.cu): *out / out[count] are set to all ones, marked
+// with the first erroneous position(s), then settled into utf8_error_info.
+cudaError_t launch_locate(const uint8_t* data, uint64_t n, utf8_error_info* out,
+                          const LaunchCfg& cfg, int sm_count, cudaStream_t st);
+cudaError_t launch_locate_batch(const uint8_t* data, const int64_t* offsets, int64_t count,
+                                utf8_error_info* out, const LaunchCfg& cfg, int sm_count,
+                                cudaStream_t st);
+// The batch pass of launch_locate_batch (batch.cu).
+cudaError_t launch_batch_first_errors(const uint8_t* data, const int64_t* offsets, int64_t count,
+                                      utf8_error_info* out, const LaunchCfg& cfg, int sm_count,
+                                      cudaStream_t st);
 
 }  // namespace utf8gpu

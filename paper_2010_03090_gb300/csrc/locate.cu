@@ -1,0 +1,129 @@
+// Error location for one buffer and for batches (see locate.cuh).
+//
+// locate_kernel streams the buffer exactly like validate_kernel (same tiles,
+// persistent grid, one contiguous run of tiles per warp, next tile prefetched)
+// and, on the first tile of its run that holds an error, takes the warp's
+// smallest erroneous position into an atomic minimum and stops: its later
+// tiles can only hold larger positions.  A one-thread kernel then settles the
+// minimum into the location.  For batches the batch pass (batch.cu) marks each
+// string's first erroneous position and one thread per string settles it.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+#include "locate.cuh"
+#include "lookup.cuh"
+#include "tiles.cuh"
+
+namespace utf8gpu {
+
+template <int ROWS>
+__global__ void __launch_bounds__(kBlockThreads)
+    locate_kernel(Span s, uint64_t tiles, utf8_error_info* out) {
+  constexpr uint64_t tb = TileGeom<ROWS>::kBytes;
+  const int lane = threadIdx.x & (kLanes - 1);
+  const uint64_t warps = (uint64_t)gridDim.x * (kBlockThreads / kLanes);
+  const uint64_t w = (uint64_t)blockIdx.x * (kBlockThreads / kLanes) + (threadIdx.x / kLanes);
+  const uint64_t t0 = tiles * w / warps;
+  const uint64_t t1 = tiles * (w + 1) / warps;
+  if (t0 >= t1) return;
+  const uint32_t merge_sel = carry_merge_selector(lane);
+  Carry carry = ascii_carry();
+  if (t0 > 0) carry = halo_carry(load_word(s, t0 * tb - 4));
+  uint64_t in0, in1;
+  interior_tiles<ROWS>(s, in0, in1);
+  const uint8_t* lane_ptr = s.abase + t0 * tb + lane * 16;
+  uint4 next[ROWS];
+  load_tile<ROWS>(s, t0, in0, in1, lane, lane_ptr, next);
+  for (uint64_t t = t0; t < t1; ++t, lane_ptr += tb) {
+    uint4 d[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) d[r] = next[r];
+    if (t + 1 < t1) load_tile<ROWS>(s, t + 1, in0, in1, lane, lane_ptr + tb, next);
+    uint32_t e[ROWS / 2][8];
+    check_tile<ROWS>(d, carry, lane, merge_sel, e);
+    uint32_t any = 0;
+#pragma unroll
+    for (int p = 0; p < ROWS / 2; ++p)
+#pragma unroll
+      for (int m = 0; m < 8; ++m) any |= e[p][m];
+    if (__any_sync(kFull, any != 0)) {
+      const uint32_t first = __reduce_min_sync(kFull, lane_first_error<ROWS>(e, lane));
+      // virtual positions before s.off are zeros after zeros: never erroneous
+      if (lane == 0) mark_first_error(out, t * tb + first - s.off);
+      return;
+    }
+  }
+}
+
+__global__ void settle_kernel(const uint8_t* data, uint64_t n, utf8_error_info* out) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) settle_location(data, n, out->position, out);
+}
+
+__global__ void settle_batch_kernel(const uint8_t* __restrict__ data,
+                                    const int64_t* __restrict__ offsets, int64_t count,
+                                    utf8_error_info* out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    const int64_t o = offsets[i];
+    settle_location(data + o, (uint64_t)(offsets[i + 1] - o), out[i].position, &out[i]);
+  }
+}
+
+template <int ROWS>
+static int locate_occupancy() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, locate_kernel<ROWS>, kBlockThreads, 0) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n > 0 ? n : 1;
+}
+
+template <int ROWS>
+static cudaError_t launch_locate_rows(const Span& s, utf8_error_info* out, int blocks_per_sm,
+                                      int sm_count, cudaStream_t st) {
+  const uint64_t tiles = span_tiles<ROWS>(s);
+  const int fit = locate_occupancy<ROWS>();
+  const int bps = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : fit;
+  const uint64_t warps_per_block = kBlockThreads / kLanes;
+  uint64_t grid = (uint64_t)sm_count * (uint64_t)bps;
+  const uint64_t need = (tiles + warps_per_block - 1) / warps_per_block;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  locate_kernel<ROWS><<<(unsigned)grid, kBlockThreads, 0, st>>>(s, tiles, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_locate(const uint8_t* data, uint64_t n, utf8_error_info* out,
+                          const LaunchCfg& cfg, int sm_count, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0xFF, sizeof(utf8_error_info), st);
+  if (e == cudaSuccess && n > 0) {
+    const Span s = make_span(data, n);
+    switch (cfg.rows) {
+      case 2: e = launch_locate_rows<2>(s, out, cfg.blocks_per_sm, sm_count, st); break;
+      case 4: e = launch_locate_rows<4>(s, out, cfg.blocks_per_sm, sm_count, st); break;
+      default: e = launch_locate_rows<8>(s, out, cfg.blocks_per_sm, sm_count, st); break;
+    }
+  }
+  if (e != cudaSuccess) return e;
+  settle_kernel<<<1, 32, 0, st>>>(data, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_locate_batch(const uint8_t* data, const int64_t* offsets, int64_t count,
+                                utf8_error_info* out, const LaunchCfg& cfg, int sm_count,
+                                cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(out, 0xFF, (size_t)count * sizeof(utf8_error_info), st);
+  if (e == cudaSuccess) e = launch_batch_first_errors(data, offsets, count, out, cfg, sm_count, st);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = (count + 255) / 256;
+  const int64_t cap = (int64_t)sm_count * 8;
+  settle_batch_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, st>>>(data, offsets,
+                                                                              count, out);
+  return cudaGetLastError();
+}
+
+}  // namespace utf8gpu

@@ -47,3 +47,47 @@ def test_all_cores_split_keeps_validity():
             assert cuts[0] == 0 and cuts[-1] == b.size and np.all(np.diff(cuts) >= 0)
             parts = oracle.valid_batch(b, cuts, threads=2)
             assert bool(parts.all()) == whole
+
+
+def test_location_rule_on_every_short_class_string():
+    """The rule the error-location kernels use (locate.cuh), restated here:
+    take the first position where the Section 6 classification reports an
+    error (the lookup aid's per-position special_cases ^ must_be_2_3, with
+    the Section 6.3 zero padding), step back at most three bytes to a
+    position where no character is cut; that is the oracle's longest valid
+    prefix, for every string over the 14 byte classes up to 4 bytes."""
+    import itertools
+    import sys
+
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import oracle
+    from oracle import lookup_aid
+
+    def first_error(b):
+        buf = np.concatenate([np.frombuffer(b, np.uint8), np.zeros(3, np.uint8)])
+        prev = np.zeros(3, np.uint8)
+        sc = lookup_aid.classify(buf, prev)["special_cases"]
+        m = lookup_aid.must_be_2_3_continuation(buf, prev)
+        nz = np.nonzero(sc ^ m)[0]
+        return int(nz[0]) if nz.size else None
+
+    def whole_characters_before(b, m):
+        c1, c2, c3 = (b[m - k] if m >= k else 0 for k in (1, 2, 3))
+        return not (c1 >= 0xC0 or c2 >= 0xE0 or c3 >= 0xF0)
+
+    reps = [0x41, 0x85, 0x95, 0xA5, 0xC0, 0xC5, 0xE0, 0xE5, 0xED, 0xEE, 0xF0, 0xF2, 0xF4, 0xF8]
+    for length in range(5):
+        for t in itertools.product(reps, repeat=length):
+            b = bytes(t)
+            p = first_error(b)
+            if p is None:
+                assert oracle.locate(b) == (len(b), 0)
+                continue
+            m = min(p, len(b))
+            steps = 0
+            while not whole_characters_before(b, m):
+                m -= 1
+                steps += 1
+            assert steps <= 3 and p - m <= 3
+            assert m == oracle.locate(b)[0], b.hex()
