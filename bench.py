@@ -59,7 +59,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--buffer-bytes", type=int, default=GIB)
     ap.add_argument("--no-extras", action="store_true", help="skip batch/serving extras")
-    ap.add_argument("--legs", default="main,e2e,cpu,batch,serve,stream,copy",
+    ap.add_argument("--legs", default="main,e2e,cpu,locate,batch,serve,stream,copy",
                     help="comma-separated legs to run (profiling runs pick one)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-memory leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
@@ -320,15 +320,20 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if args.no_cpu:
         legs.discard("cpu")
     if args.no_extras:
-        legs -= {"batch", "serve", "stream", "copy"}
+        legs -= {"locate", "batch", "serve", "stream", "copy"}
     if "main" not in legs:  # a single secondary leg (profiling runs)
         torch.cuda.set_device(local_rank)
         u.lib()
         out = {}
+        if "locate" in legs:
+            host, names = make_workload(args.buffer_bytes, 0, args.variants.split(","))
+            dev = [torch.from_numpy(b).cuda() for b in host]
+            out["locate"] = bench_locate(u, torch, dev, names, torch.cuda.Stream())
+            del dev
         if "batch" in legs:
             out["batched_1m"] = bench_batch(u, torch, torch.cuda.Stream(),
                                             float(measured_peaks().get("hbm_gbs") or FALLBACK_HBM_GBS),
-                                            args.per_string_sample)
+                                            args.per_string_sample, "locate" in legs)
         if "serve" in legs:
             out["serving"] = bench_serving(torch, args.serve_seconds)
         if "stream" in legs:
@@ -475,11 +480,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     }
     if world == 1 and "cpu" in legs:
         line["cpu_baseline"] = oracle_baseline(host, names, args.cpu_seconds)
+    if world == 1 and "locate" in legs:
+        line["locate"] = bench_locate(u, torch, dev, names, stream, flags)
     if world == 1 and legs & {"batch", "serve", "stream", "copy"}:
         del dev
         torch.cuda.empty_cache()
         if "batch" in legs:
-            line["batched_1m"] = bench_batch(u, torch, stream, peak, args.per_string_sample)
+            line["batched_1m"] = bench_batch(u, torch, stream, peak, args.per_string_sample,
+                                             "locate" in legs)
         if "serve" in legs:
             line["serving"] = bench_serving(torch, args.serve_seconds)
         if "stream" in legs:
@@ -492,8 +500,44 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         dist.destroy_process_group()
 
 
-def bench_batch(u, torch, stream, peak: float, sample: int = 20000) -> dict:
-    """1M strings in one batch vs one launch per string (a sample)."""
+def bench_locate(u, torch, dev, names, stream, flags=None, steps: int = 30) -> dict:
+    """utf8_locate_error_async on the main leg's buffers (one memset and two
+    kernels per buffer: the lookup pass and the one-thread settle), against
+    the main leg's flags: rule 0 exactly for the valid buffers, rule b (too
+    short) in the last 3 bytes for the truncated tails."""
+    outs = torch.empty((len(dev), 2), dtype=torch.int64, device="cuda")
+
+    def one_step():
+        for i, t in enumerate(dev):
+            u.utf8_locate_error_async(t, outs[i], stream=stream)
+
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            one_step()
+        a.record(stream)
+        for _ in range(steps):
+            one_step()
+        b.record(stream)
+    stream.synchronize()
+    ms = a.elapsed_time(b)
+    total = sum(t.numel() for t in dev) * steps
+    pos, rule = u.error_info_fields(outs)
+    pos, rule = pos.cpu().numpy().tolist(), rule.cpu().numpy().tolist()
+    sizes = [t.numel() for t in dev]
+    ok = all((r == 0 and p == n) or (r == 2 and n - 3 <= p < n)
+             for p, r, n in zip(pos, rule, sizes))
+    if flags is not None:
+        ok = ok and all((r == 0) == bool(f) for r, f in zip(rule, flags))
+    return {"gbs": round(total / (ms / 1e3) / 1e9, 1), "steps": steps,
+            "bytes_per_step": int(sum(sizes)), "kernels_per_buffer": 2,
+            "rules": dict(zip(names, rule)), "results_consistent": ok}
+
+
+def bench_batch(u, torch, stream, peak: float, sample: int = 20000,
+                locate: bool = False) -> dict:
+    """1M strings in one batch vs one launch per string (a sample); with
+    `locate`, also utf8_locate_errors_batch on the same batch."""
     import synth
     data, offsets, _ = synth.workload_batch_1m()
     d = torch.from_numpy(data).cuda()
@@ -525,12 +569,27 @@ def bench_batch(u, torch, stream, peak: float, sample: int = 20000) -> dict:
         stream.synchronize()
         per_ms = (time.perf_counter() - t) * 1e3
     per_gbs = int(offsets[sample] - offsets[0]) / (per_ms / 1e3) / 1e9
-    return {"strings": int(offsets.size - 1), "bytes": int(data.size),
-            "ms": round(ms, 4), "gbs": round(batch_gbs, 1),
-            "pct_of_hbm_peak": round(100 * moved / (ms / 1e3) / 1e9 / peak, 1),
-            "per_string_launch_gbs": round(per_gbs, 3),
-            "per_string_launch_sample": sample,
-            "speedup_vs_per_string": round(batch_gbs / per_gbs, 1)}
+    res = {"strings": int(offsets.size - 1), "bytes": int(data.size),
+           "ms": round(ms, 4), "gbs": round(batch_gbs, 1),
+           "pct_of_hbm_peak": round(100 * moved / (ms / 1e3) / 1e9 / peak, 1),
+           "per_string_launch_gbs": round(per_gbs, 3),
+           "per_string_launch_sample": sample,
+           "speedup_vs_per_string": round(batch_gbs / per_gbs, 1)}
+    if locate:
+        info = torch.empty((offsets.size - 1, 2), dtype=torch.int64, device="cuda")
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                u.utf8_locate_errors_batch(d, o, info, stream=stream)
+            a.record(stream)
+            for _ in range(reps):
+                u.utf8_locate_errors_batch(d, o, info, stream=stream)
+            b.record(stream)
+        stream.synchronize()
+        lms = a.elapsed_time(b) / reps
+        _, rule = u.error_info_fields(info)
+        res["locate"] = {"ms": round(lms, 4), "gbs": round(data.size / (lms / 1e3) / 1e9, 1),
+                         "rules_match_flags": bool(torch.equal(rule == 0, out == 1))}
+    return res
 
 
 def bench_stream(u, torch) -> dict:
