@@ -36,16 +36,29 @@
 
 namespace utf8gpu {
 
-// Bytes [x, x + 4) of `data` (absolute offsets), zero outside [lo, hi).
-__device__ __forceinline__ uint32_t gather4(const uint8_t* data, int64_t x, int64_t lo,
-                                            int64_t hi) {
-  uint32_t w = 0;
+// The 8 bytes [x, x + 8) of `data` (absolute offsets) as two words, bytes
+// outside [lo, hi) zero.  Only the aligned 4-byte words holding a byte of
+// [lo, hi) are read; [lo, hi) lies inside the batch region, so those words lie
+// in granules the stream reads anyway.
+__device__ __forceinline__ void gather8(const uint8_t* data, int64_t x, int64_t lo, int64_t hi,
+                                        uint32_t& w_lo, uint32_t& w_hi) {
+  const int64_t a = lo > x ? lo : x;
+  const int64_t b = hi < x + 8 ? hi : x + 8;
+  w_lo = w_hi = 0u;
+  if (a >= b) return;
+  const uintptr_t px = reinterpret_cast<uintptr_t>(data + x);
+  const int sh = (int)(px & 3u);
+  const uint32_t* base = reinterpret_cast<const uint32_t*>(px - (uintptr_t)sh);
+  uint32_t u[3];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int64_t y = x + k;
-    if (y >= lo && y < hi) w |= (uint32_t)__ldg(data + y) << (8 * k);
+  for (int k = 0; k < 3; ++k) {
+    const int64_t ws = x - sh + 4 * k;  // word k holds bytes [ws, ws + 4)
+    u[k] = (ws < b && ws + 4 > a) ? __ldg(base + k) : 0u;
   }
-  return w;
+  const uint32_t s8 = 8u * (uint32_t)sh;
+  const int ka = (int)(a - x), kb = (int)(b - x);
+  w_lo = __funnelshift_r(u[0], u[1], s8) & keep_bytes(ka, kb);
+  w_hi = __funnelshift_r(u[1], u[2], s8) & keep_bytes(ka - 4, kb - 4);
 }
 
 // First j in [lo, hi) with offsets[j] >= target (hi if none); whole warp.
@@ -103,30 +116,67 @@ __global__ void __launch_bounds__(kBlockThreads)
   const int64_t b0 = warp_lower_bound(offsets, 0, count + 1, range_lo);
   const int64_t b1 = warp_lower_bound(offsets, b0, count + 1, range_hi);
   // strings that can hold a position of this warp: b0 - 1 .. b1 - 1
-  const int64_t own_lo = b0 > 0 ? b0 - 1 : 0;
   const int64_t own_hi = b1 < count ? b1 : count;
+
+  __shared__ uint32_t err_smem[kBlockThreads / kLanes][ROWS / 2 * 8 * kLanes];
+  uint32_t* err_words = err_smem[threadIdx.x / kLanes];
 
   const uint32_t merge_sel = carry_merge_selector(lane);
   Carry carry = ascii_carry();
   if (t0 > 0) carry = halo_carry(load_word(region, t0 * kTileBytes - 4));
+  // Tiles are counted from t0 in 32 bits (a warp's run is far below 2^32
+  // tiles); [r_in0, r_in1) are its tiles wholly inside the region.
+  const uint32_t n_tiles = (uint32_t)(t1 - t0);
   uint64_t in0, in1;
   interior_tiles<ROWS>(region, in0, in1);
+  const uint32_t r_in0 = (uint32_t)(in0 <= t0 ? 0 : (in0 - t0 < n_tiles ? in0 - t0 : n_tiles));
+  const uint32_t r_in1 = (uint32_t)(in1 <= t0 ? 0 : (in1 - t0 < n_tiles ? in1 - t0 : n_tiles));
   const uint8_t* lane_ptr = region.abase + t0 * kTileBytes + lane * 16;
-  int64_t next_group = b0;  // first boundary not yet checked
-  int64_t group_last = (next_group + kLanes < b1 ? next_group + kLanes : b1) - 1;
-  int64_t group_last_off = next_group < b1 ? offsets[group_last] : 0;
+
+  // Boundary groups of up to 32, [next_group, group_last]; lane k holds
+  // g_off = offsets[next_group + k] (INT64_MAX past the group) and every lane
+  // holds prev_off = offsets[next_group - 1].  A group is checked on the tile
+  // holding its last boundary (tile `due`, counted from t0) or on the warp's
+  // last tile, so its bytes are recent in L2.
+  // The offsets of the group after the open one are loaded when it opens
+  // (g_nxt), so opening a group waits for no load.
+  int64_t next_group = b0;
+  int64_t group_last = -1;
+  int64_t g_off = INT64_MAX;
+  int64_t prev_off = b0 > 0 ? offsets[b0 - 1] : INT64_MIN;
+  uint32_t due = 0xFFFFFFFFu;
+  auto group_offsets = [&](int64_t first) -> int64_t {
+    const int64_t last = (first + kLanes < b1 ? first + kLanes : b1) - 1;
+    return first + lane <= last ? offsets[first + lane] : INT64_MAX;
+  };
+  int64_t g_nxt = b0 < b1 ? group_offsets(b0) : INT64_MAX;
+  auto open_group = [&]() {
+    if (next_group < b1) {
+      group_last = (next_group + kLanes < b1 ? next_group + kLanes : b1) - 1;
+      g_off = g_nxt;
+      const int64_t last_off = __shfl_sync(kFull, g_off, (int)(group_last - next_group));
+      due = (uint32_t)(((uint64_t)(last_off - vbase) / kTileBytes) - t0);
+      g_nxt = group_last + 1 < b1 ? group_offsets(group_last + 1) : INT64_MAX;
+    } else {
+      g_off = INT64_MAX;
+      due = 0xFFFFFFFFu;
+    }
+  };
+  open_group();
+
   uint4 next[ROWS];  // the next tile's loads, issued one tile ahead
-  load_tile<ROWS>(region, t0, in0, in1, lane, lane_ptr, next);
+  if (r_in0 == 0 && r_in1 > 0) load_tile_interior<ROWS>(lane_ptr, next);
+  else load_tile_checked<ROWS>(region, t0, lane, next);
 
-  for (uint64_t t = t0; t < t1; ++t, lane_ptr += kTileBytes) {
-    const int64_t tile_lo = vbase + (int64_t)(t * kTileBytes);
-    const int64_t tile_hi = tile_lo + (int64_t)kTileBytes;
-
+  for (uint32_t i = 0; i < n_tiles; ++i, lane_ptr += kTileBytes) {
     // ---- stream the tile (plain `lookup` over the concatenation) ----------
     uint4 d[ROWS];
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) d[r] = next[r];
-    if (t + 1 < t1) load_tile<ROWS>(region, t + 1, in0, in1, lane, lane_ptr + kTileBytes, next);
+    if (i + 1 < n_tiles) {
+      if (i + 1 >= r_in0 && i + 1 < r_in1) load_tile_interior<ROWS>(lane_ptr + kTileBytes, next);
+      else load_tile_checked<ROWS>(region, t0 + i + 1, lane, next);
+    }
     uint32_t e[ROWS / 2][8];
     check_tile<ROWS>(d, carry, lane, merge_sel, e);
     uint32_t any_err = 0;
@@ -136,49 +186,98 @@ __global__ void __launch_bounds__(kBlockThreads)
       for (int m = 0; m < 8; ++m) any_err |= e[p][m];
 
     // ---- charge streamed errors to strings (only where errors exist) -----
+    // Boundaries before next_group lie before this tile, so a position p of
+    // the tile belongs to string next_group - 1 + (number of the open group's
+    // boundaries <= p), one ballot over g_off, unless p lies past the group's
+    // last boundary (then a binary search).  The warp takes the error bytes
+    // one at a time: they go through shared memory so that each lane walks
+    // its own in one rolled loop.
     if (__any_sync(kFull, any_err != 0)) {
+      const int64_t tile_lo = vbase + (int64_t)((t0 + i) * kTileBytes);
+      static_assert(ROWS / 2 * 8 <= 32, "one bit per error word");
+      uint32_t nonzero = 0;  // bit w: error word w of this lane is non-zero
 #pragma unroll
-      for (int pr = 0; pr < ROWS / 2; ++pr) {
+      for (int pr = 0; pr < ROWS / 2; ++pr)
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
-          uint32_t bits = e[pr][m];
-          while (bits != 0) {
-            const int byte = (__ffs(bits) - 1) >> 3;
-            bits &= ~(0xFFu << (8 * byte));
-            const int64_t p = tile_lo + (int64_t)interleaved_position<ROWS>(pr, m, byte, lane);
-            const int64_t own = last_at_most(offsets, own_lo, own_hi + 1, p);
-            if (own >= 0 && own < count && p - offsets[own] >= 3 && p < offsets[own + 1])
-              charge<LOCATE>(out_valid, out_err, own, p - offsets[own]);
+          err_words[(pr * 8 + m) * kLanes + lane] = e[pr][m];
+          nonzero |= (e[pr][m] != 0 ? 1u : 0u) << (pr * 8 + m);
+        }
+      __syncwarp();
+      const int gsize = next_group < b1 ? (int)(group_last - next_group + 1) : 0;
+      int k = 0;
+      uint32_t bits = 0;
+      for (;;) {
+        // this lane's next error byte, if any
+        if (bits == 0 && nonzero != 0) {
+          k = __ffs(nonzero) - 1;
+          nonzero &= nonzero - 1;
+          bits = err_words[k * kLanes + lane];
+        }
+        int64_t p = INT64_MAX;
+        if (bits != 0) {
+          const int byte = (__ffs(bits) - 1) >> 3;
+          bits &= ~(0xFFu << (8 * byte));
+          p = tile_lo + (int64_t)interleaved_position<ROWS>(k >> 3, k & 7, byte, lane);
+        }
+        uint32_t pending = __ballot_sync(kFull, p != INT64_MAX);
+        if (pending == 0) break;
+        while (pending != 0) {
+          const int src = __ffs(pending) - 1;
+          pending &= pending - 1;
+          const int64_t q = __shfl_sync(kFull, p, src);
+          const int cnt = __popc(__ballot_sync(kFull, g_off <= q));
+          const int64_t lo_cnt = __shfl_sync(kFull, g_off, cnt > 0 ? cnt - 1 : 0);
+          if (lane == src) {
+            int64_t own, o_lo, o_hi;
+            if (cnt < gsize || gsize == 0) {
+              own = next_group - 1 + cnt;
+              o_lo = cnt > 0 ? lo_cnt : prev_off;
+              o_hi = INT64_MAX;  // the next boundary lies past q
+            } else {
+              own = last_at_most(offsets, group_last, own_hi + 1, q);
+              o_lo = own >= 0 && own <= count ? offsets[own] : 0;
+              o_hi = own >= 0 && own < count ? offsets[own + 1] : 0;
+            }
+            if (own >= 0 && own < count && q - o_lo >= 3 && q < o_hi)
+              charge<LOCATE>(out_valid, out_err, own, q - o_lo);
           }
         }
       }
+      __syncwarp();
     }
 
     // ---- boundaries: exact head and tail checks, 32 at a time ------------
-    // A group is checked once the stream has passed its last boundary (its
-    // bytes are then recent in L2), or at the end of the warp's range.
-    while (next_group < b1) {
-      const int64_t last = group_last;
-      if (t + 1 < t1 && group_last_off >= tile_hi) break;
+    // Lane k takes boundary j = next_group + k at o_j: the tail of string
+    // j-1, [o_{j-1}, o_j), and the head of string j, [o_j, o_{j+1}).  The
+    // neighbouring offsets come from the neighbouring lanes.
+    while (i >= due || (i + 1 == n_tiles && next_group < b1)) {
       const int64_t j = next_group + lane;
-      if (j <= last) {
-        const int64_t oj = offsets[j];
-        if (j >= 1) {  // tail of string j-1, which ends at oj
-          const int64_t s = offsets[j - 1];
-          const WordLut tail = lut_word(gather4(data, oj - 4, s, oj));
-          const uint32_t te = word_error(tail, ascii_lut());  // positions oj .. oj+3
-          if (te != 0) charge<LOCATE>(out_valid, out_err, j - 1, oj - s + ((__ffs(te) - 1) >> 3));
+      const bool act = j <= group_last;
+      const int64_t oj = g_off;
+      int64_t o_prev = __shfl_up_sync(kFull, oj, 1);
+      int64_t o_next = __shfl_down_sync(kFull, oj, 1);
+      if (lane == 0) o_prev = prev_off;
+      if (act && j == group_last && j < count) o_next = offsets[j + 1];
+      if (act) {
+        const int64_t lo = j >= 1 ? o_prev : oj;
+        const int64_t hi = j < count ? o_next : oj;
+        uint32_t w_tail, w_head;  // bytes [o_j - 4, o_j) and [o_j, o_j + 4), in [lo, hi)
+        gather8(data, oj - 4, lo, hi, w_tail, w_head);
+        WordLut tail, head;
+        lut_pair(w_tail, w_head, tail, head);
+        if (j >= 1) {  // positions o_j .. o_j+3 after string j-1 (virtual zeros)
+          const uint32_t te = word_error(tail, ascii_lut());
+          if (te != 0) charge<LOCATE>(out_valid, out_err, j - 1, oj - lo + ((__ffs(te) - 1) >> 3));
         }
-        if (j < count) {  // head of string j, which starts at oj
-          const int64_t end = offsets[j + 1];
-          const WordLut head = lut_word(gather4(data, oj, oj, end));
-          const uint32_t he = word_error(ascii_lut(), head);  // positions oj .. oj+3
+        if (j < count) {  // positions o_j .. o_j+3 of string j (zeros before it)
+          const uint32_t he = word_error(ascii_lut(), head);
           if (he != 0) charge<LOCATE>(out_valid, out_err, j, (__ffs(he) - 1) >> 3);
         }
       }
-      next_group = last + 1;
-      group_last = (next_group + kLanes < b1 ? next_group + kLanes : b1) - 1;
-      if (next_group < b1) group_last_off = offsets[group_last];
+      prev_off = __shfl_sync(kFull, g_off, (int)(group_last - next_group));
+      next_group = group_last + 1;
+      open_group();
     }
   }
 }
@@ -199,6 +298,8 @@ cudaError_t launch_batch(const uint8_t* data, const int64_t* offsets, int64_t co
   cudaError_t e = cudaMemsetAsync(out_valid, 1, (size_t)count, st);
   if (e != cudaSuccess) return e;
   switch (cfg.batch_rows) {
+    case 8: return launch_batch_rows<8>(data, offsets, count, out_valid, cfg.batch_blocks_per_sm,
+                                        sm_count, st);
     case 4: return launch_batch_rows<4>(data, offsets, count, out_valid, cfg.batch_blocks_per_sm,
                                         sm_count, st);
     default: return launch_batch_rows<2>(data, offsets, count, out_valid, cfg.batch_blocks_per_sm,
@@ -211,6 +312,8 @@ cudaError_t launch_batch_first_errors(const uint8_t* data, const int64_t* offset
                                       cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   switch (cfg.batch_rows) {
+    case 8: return launch_batch_rows<8, true>(data, offsets, count, nullptr,
+                                              cfg.batch_blocks_per_sm, sm_count, st, out);
     case 4: return launch_batch_rows<4, true>(data, offsets, count, nullptr,
                                               cfg.batch_blocks_per_sm, sm_count, st, out);
     default: return launch_batch_rows<2, true>(data, offsets, count, nullptr,
@@ -226,6 +329,7 @@ int batch_blocks_per_sm(int rows) {
   int n = 0;
   cudaError_t e;
   switch (rows) {
+    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<8, false>, kBlockThreads, 0); break;
     case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<4, false>, kBlockThreads, 0); break;
     default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<2, false>, kBlockThreads, 0); break;
   }

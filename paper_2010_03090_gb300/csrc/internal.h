@@ -13,7 +13,7 @@ constexpr int kBlockThreads = 256;
 struct LaunchCfg {
   int rows = 8;           // tile rows per warp (tile = rows * 512 bytes): 2, 4 or 8
   int blocks_per_sm = 8;  // resident CTAs per SM in the persistent grid
-  int batch_rows = 4;     // tile rows for the batch kernel
+  int batch_rows = 8;     // tile rows for the batch kernel: 2, 4 or 8
   int batch_blocks_per_sm = 8;
 };
 

@@ -111,7 +111,7 @@ LaunchCfg tuned_config(const char* gpu_name, int sm_count) {
 
 void clamp_to_occupancy(LaunchCfg& cfg) {
   if (cfg.rows != 2 && cfg.rows != 4 && cfg.rows != 8) cfg.rows = 8;
-  if (cfg.batch_rows != 2 && cfg.batch_rows != 4) cfg.batch_rows = 4;
+  if (cfg.batch_rows != 2 && cfg.batch_rows != 4 && cfg.batch_rows != 8) cfg.batch_rows = 8;
   const int v = validate_blocks_per_sm(cfg.rows);
   const int b = batch_blocks_per_sm(cfg.batch_rows);
   if (cfg.blocks_per_sm < 1 || cfg.blocks_per_sm > v) cfg.blocks_per_sm = v;
@@ -180,7 +180,7 @@ int run_autotune(int flags) {
   if (e == cudaSuccess) {
     float best_single = 1e30f, best_batch = 1e30f;
     const int rows_c[3] = {2, 4, 8};
-    const int brows_c[2] = {2, 4};
+    const int brows_c[3] = {2, 4, 8};
     const int bps_c[4] = {2, 4, 6, 8};
     for (int r = 0; r < 3; ++r)
       for (int k = 0; k < 4; ++k) {
@@ -191,7 +191,7 @@ int run_autotune(int flags) {
         const float ms = time_ms(st, a, b, 10, c, sms, false, data, bytes, offsets, count, out);
         if (ms < best_single) { best_single = ms; best.rows = c.rows; best.blocks_per_sm = c.blocks_per_sm; }
       }
-    for (int r = 0; r < 2; ++r)
+    for (int r = 0; r < 3; ++r)
       for (int k = 0; k < 4; ++k) {
         LaunchCfg c = best;
         c.batch_rows = brows_c[r];
