@@ -621,6 +621,31 @@ def bench_stream(u, torch) -> dict:
             torch.cuda.synchronize()
             res[f"chunk_{chunk >> 20}MiB_gbs"] = round(d.numel() * reps / (a.elapsed_time(b) / 1e3) / 1e9, 1)
             res[f"chunk_{chunk >> 20}MiB_valid"] = int(out.item())
+        # the same sequence captured once in a CUDA graph and replayed: the
+        # kernels without the per-call host cost of the loop above
+        for chunk in (1 << 20, 16 << 20):
+            views = [d[i:i + chunk] for i in range(0, d.numel(), chunk)]
+            g_stream = torch.cuda.Stream()
+            g = torch.cuda.CUDAGraph()
+            out.zero_()
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=g_stream):
+                u.utf8_stream_reset(h, stream=g_stream)
+                for v in views:
+                    u.utf8_stream_update(h, v, stream=g_stream)
+                u.utf8_stream_finish(h, out, stream=g_stream)
+            g.replay()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 5
+            a.record()
+            for _ in range(reps):
+                g.replay()
+            b.record()
+            torch.cuda.synchronize()
+            res[f"chunk_{chunk >> 20}MiB_graph_gbs"] = round(d.numel() * reps / (a.elapsed_time(b) / 1e3) / 1e9, 1)
+            res[f"chunk_{chunk >> 20}MiB_graph_valid"] = int(out.item())
+            del g
     finally:
         u.utf8_stream_destroy(h)
     one = torch.zeros(1, dtype=torch.uint8, device="cuda")

@@ -193,7 +193,11 @@ int utf8_validate_chunk(const uint8_t* data, size_t len, uint32_t prefix, int pr
  * update validates the next chunk (device memory; asynchronous; chunks may be
  * reused buffers, the state keeps what it needs), finish checks the end of the
  * stream and writes the result (1 = valid) to the device byte *out_valid.
- * Calls on one state must be ordered (same stream, or synchronised).
+ * Calls on one state must be ordered (same stream, or synchronised).  Apart
+ * from create and destroy none of them allocates or synchronises, so a whole
+ * sequence reset, updates, finish can be captured in one CUDA graph and
+ * replayed (which device slot each update uses is fixed when it is captured;
+ * do not mix replays with direct calls on the same state).
  */
 typedef struct utf8_stream utf8_stream;
 utf8_stream* utf8_stream_create(void);

@@ -49,14 +49,14 @@ __device__ __forceinline__ void gather8(const uint8_t* data, int64_t x, int64_t 
   const uintptr_t px = reinterpret_cast<uintptr_t>(data + x);
   const int sh = (int)(px & 3u);
   const uint32_t* base = reinterpret_cast<const uint32_t*>(px - (uintptr_t)sh);
+  const int ka = (int)(a - x), kb = (int)(b - x);  // wanted bytes [ka, kb) of the 8, 0 <= ka < kb <= 8
   uint32_t u[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const int64_t ws = x - sh + 4 * k;  // word k holds bytes [ws, ws + 4)
-    u[k] = (ws < b && ws + 4 > a) ? __ldg(base + k) : 0u;
+    const int ws = 4 * k - sh;  // word k holds bytes [ws, ws + 4) of the 8
+    u[k] = (ws < kb && ws + 4 > ka) ? __ldg(base + k) : 0u;
   }
   const uint32_t s8 = 8u * (uint32_t)sh;
-  const int ka = (int)(a - x), kb = (int)(b - x);
   w_lo = __funnelshift_r(u[0], u[1], s8) & keep_bytes(ka, kb);
   w_hi = __funnelshift_r(u[1], u[2], s8) & keep_bytes(ka - 4, kb - 4);
 }
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     // neighbouring offsets come from the neighbouring lanes.
     while (i >= due || (i + 1 == n_tiles && next_group < b1)) {
       const int64_t j = next_group + lane;
-      const bool act = j <= group_last;
+      const bool act = lane <= (int)(group_last - next_group);
       const int64_t oj = g_off;
       int64_t o_prev = __shfl_up_sync(kFull, oj, 1);
       int64_t o_next = __shfl_down_sync(kFull, oj, 1);

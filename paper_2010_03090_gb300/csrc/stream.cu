@@ -54,6 +54,8 @@ __device__ __forceinline__ void mask_positions(uint32_t (&e)[ROWS / 2][8], uint6
       }
 }
 
+constexpr int kChunkRows = 8;  // tile rows per warp (4 KiB tiles), as the single-buffer default
+
 template <int ROWS>
 __global__ void __launch_bounds__(kBlockThreads) chunk_kernel(Span s, uint64_t tiles, ChunkArgs a) {
   constexpr uint64_t tb = TileGeom<ROWS>::kBytes;
@@ -85,9 +87,13 @@ __global__ void __launch_bounds__(kBlockThreads) chunk_kernel(Span s, uint64_t t
   interior_tiles<ROWS>(s, in0, in1);
   const uint8_t* lane_ptr = s.abase + t0 * tb + lane * 16;
   uint32_t err = 0;
+  uint4 next[ROWS];  // the next tile's loads, issued one tile ahead
+  load_tile<ROWS>(s, t0, in0, in1, lane, lane_ptr, next);
   for (uint64_t t = t0; t < t1; ++t, lane_ptr += tb) {
     uint4 d[ROWS];
-    load_tile<ROWS>(s, t, in0, in1, lane, lane_ptr, d);
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) d[r] = next[r];
+    if (t + 1 < t1) load_tile<ROWS>(s, t + 1, in0, in1, lane, lane_ptr + tb, next);
     if (t == 0 && lane == 0) {
       // prefix byte i (data offset i - 4) sits at virtual position off + i - 4
 #pragma unroll
@@ -113,14 +119,29 @@ __global__ void __launch_bounds__(kBlockThreads) chunk_kernel(Span s, uint64_t t
   if (__any_sync(kFull, err != 0) && lane == 0) *a.out_valid = 0;
 }
 
+// Resident CTAs per SM of chunk_kernel (the same on every GPU of this
+// architecture; computed once, thread-safely).
+static int chunk_blocks_per_sm() {
+  static const int n = [] {
+    int k = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, chunk_kernel<kChunkRows>, kBlockThreads,
+                                                      0) != cudaSuccess) {
+      cudaGetLastError();
+      k = 1;
+    }
+    return k > 0 ? k : 1;
+  }();
+  return n;
+}
+
 cudaError_t launch_chunk(const uint8_t* data, uint64_t n, uint32_t prefix,
                          const uint8_t* prefix_dev, int final_chunk, uint8_t* out_valid,
                          uint8_t* tail_out, int sm_count, cudaStream_t st) {
-  constexpr int ROWS = 4;
+  constexpr int ROWS = kChunkRows;
   const Span s = make_span(data, n);
   const uint64_t tiles = span_tiles<ROWS>(s);
   const uint64_t warps_per_block = kBlockThreads / kLanes;
-  uint64_t grid = (uint64_t)sm_count * 3;
+  uint64_t grid = (uint64_t)sm_count * (uint64_t)chunk_blocks_per_sm();
   const uint64_t need = (tiles + warps_per_block - 1) / warps_per_block;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;

@@ -109,3 +109,35 @@ def test_shards_share_one_flag():
                                   flag, stream=st)
         torch.cuda.synchronize()
         assert flag.item() == oracle.valid(b)
+
+
+def test_stream_sequence_in_cuda_graph():
+    """reset, a run of updates and finish captured once in a CUDA graph and
+    replayed: the replays follow the bytes in the buffer at replay time."""
+    n, chunk = 3 << 20, 256 << 10
+    buf = synth.fill(n, synth.CJK, seed=31)
+    d = torch.from_numpy(buf).cuda()
+    out = torch.zeros(1, dtype=torch.uint8, device="cuda")
+    h = u.utf8_stream_create()
+    try:
+        s = torch.cuda.Stream()
+        u.utf8_stream_reset(h, stream=s)  # first calls outside capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            u.utf8_stream_reset(h, stream=s)
+            for i in range(0, n, chunk):
+                u.utf8_stream_update(h, d[i:i + chunk], stream=s)
+            u.utf8_stream_finish(h, out, stream=s)
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(out.item()) == 1 == oracle.valid(buf)
+        bad = buf.copy()
+        synth.inject_any(bad, "surrogate", np.random.default_rng(3), at=5 * chunk - 1)
+        d.copy_(torch.from_numpy(bad))
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(out.item()) == int(oracle.valid(bad)) == 0
+    finally:
+        u.utf8_stream_destroy(h)
