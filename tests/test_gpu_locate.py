@@ -205,3 +205,24 @@ def test_invalid_arguments():
         u.utf8_locate_error((host.ctypes.data, host.size))
     assert e.value.code == 1
     assert u.utf8_locate_error(t[:0]) == (0, 0)
+
+
+def test_buffer_beyond_4gib():
+    """A single 4.5 GiB buffer (positions past 2^32): validity and error
+    location of the clean buffer and with an error past 4 GiB, in the launch
+    configuration the benchmark uses; the oracle scans the same bytes."""
+    n = (9 << 29) + 12345
+    buf = synth.fill(n, synth.CJK, seed=99)
+    t = dev(buf)
+    assert u.utf8_validate(t) == oracle.valid(buf) == True  # noqa: E712
+    assert u.utf8_locate_error(t) == (n, 0)
+    rng = np.random.default_rng(4)
+    at = (1 << 32) + 1000003
+    window = buf[at - 64:at + 64].copy()
+    synth.inject_any(window, "overlong", rng, at=64)
+    t[at - 64:at + 64] = dev(window)
+    buf[at - 64:at + 64] = window
+    want = oracle.locate(buf)
+    assert want[0] > (1 << 32) and want[1] == 4
+    assert u.utf8_validate(t) == oracle.valid(buf) == False  # noqa: E712
+    assert u.utf8_locate_error(t) == want
