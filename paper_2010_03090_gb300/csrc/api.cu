@@ -50,6 +50,7 @@ struct DeviceState {
   std::once_flag once;
   int init_error = cudaSuccess;
   int sm_count = 0;
+  std::mutex cfg_mu;  // guards cfg: the autotuner and cache loads replace it
   LaunchCfg cfg;
   uint8_t* d_results = nullptr;  // kResultSlots result bytes
   uint8_t* h_results = nullptr;  // pinned mirror
@@ -101,6 +102,12 @@ DeviceState* device() {
   return &d;
 }
 
+// The device's launch configuration, copied under its lock.
+LaunchCfg config_of(DeviceState& d) {
+  std::lock_guard<std::mutex> lock(d.cfg_mu);
+  return d.cfg;
+}
+
 bool is_device_memory(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -119,14 +126,16 @@ int set_thread_status(int status) { return set_status(status); }
 
 LaunchCfg current_config() {
   DeviceState* d = device();
-  return d ? d->cfg : LaunchCfg();
+  return d ? config_of(*d) : LaunchCfg();
 }
 
 void set_current_config(const LaunchCfg& cfg) {
   DeviceState* d = device();
   if (d) {
-    d->cfg = cfg;
-    clamp_to_occupancy(d->cfg);
+    LaunchCfg c = cfg;
+    clamp_to_occupancy(c);
+    std::lock_guard<std::mutex> lock(d->cfg_mu);
+    d->cfg = c;
   }
 }
 
@@ -148,7 +157,7 @@ bool utf8_validate(const uint8_t* data, size_t len, cudaStream_t stream) {
   if (!d) return false;
   if (!is_device_memory(data)) return set_status(UTF8_ERR_INVALID_ARG), false;
   const uint32_t slot = d->next_slot.fetch_add(1) % kResultSlots;
-  cudaError_t e = launch_validate(data, len, d->d_results + slot, d->cfg, d->sm_count, stream);
+  cudaError_t e = launch_validate(data, len, d->d_results + slot, config_of(*d), d->sm_count, stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d->h_results + slot, d->d_results + slot, 1, cudaMemcpyDeviceToHost,
                         stream);
@@ -167,7 +176,7 @@ int utf8_validate_async(const uint8_t* data, size_t len, uint8_t* out_valid,
   if (!is_device_memory(out_valid) || (len > 0 && !is_device_memory(data)))
     return set_status(UTF8_ERR_INVALID_ARG);
   if (len == 0) return cuda_status(cudaMemsetAsync(out_valid, 1, 1, stream));
-  return cuda_status(launch_validate(data, len, out_valid, d->cfg, d->sm_count, stream));
+  return cuda_status(launch_validate(data, len, out_valid, config_of(*d), d->sm_count, stream));
 }
 
 int utf8_validate_batch(const uint8_t* data, const int64_t* offsets, int64_t count,
@@ -180,7 +189,7 @@ int utf8_validate_batch(const uint8_t* data, const int64_t* offsets, int64_t cou
   if (!d) return UTF8_ERR_CUDA;
   if (!is_device_memory(data) || !is_device_memory(offsets) || !is_device_memory(out_valid))
     return set_status(UTF8_ERR_INVALID_ARG);
-  return cuda_status(launch_batch(data, offsets, count, out_valid, d->cfg, d->sm_count, stream));
+  return cuda_status(launch_batch(data, offsets, count, out_valid, config_of(*d), d->sm_count, stream));
 }
 
 int utf8_locate_error_async(const uint8_t* data, size_t len, utf8_error_info* out,
@@ -192,7 +201,7 @@ int utf8_locate_error_async(const uint8_t* data, size_t len, utf8_error_info* ou
   if (!d) return UTF8_ERR_CUDA;
   if (!is_device_memory(out) || (len > 0 && !is_device_memory(data)))
     return set_status(UTF8_ERR_INVALID_ARG);
-  return cuda_status(launch_locate(data, len, out, d->cfg, d->sm_count, stream));
+  return cuda_status(launch_locate(data, len, out, config_of(*d), d->sm_count, stream));
 }
 
 int utf8_locate_error(const uint8_t* data, size_t len, utf8_error_info* out_host,
@@ -208,7 +217,7 @@ int utf8_locate_error(const uint8_t* data, size_t len, utf8_error_info* out_host
   if (!d) return UTF8_ERR_CUDA;
   if (!is_device_memory(data)) return set_status(UTF8_ERR_INVALID_ARG);
   const uint32_t slot = d->next_info.fetch_add(1) % kInfoSlots;
-  cudaError_t e = launch_locate(data, len, d->d_info + slot, d->cfg, d->sm_count, stream);
+  cudaError_t e = launch_locate(data, len, d->d_info + slot, config_of(*d), d->sm_count, stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d->h_info + slot, d->d_info + slot, sizeof(utf8_error_info),
                         cudaMemcpyDeviceToHost, stream);
@@ -229,7 +238,7 @@ int utf8_locate_errors_batch(const uint8_t* data, const int64_t* offsets, int64_
   if (!d) return UTF8_ERR_CUDA;
   if (!is_device_memory(data) || !is_device_memory(offsets) || !is_device_memory(out))
     return set_status(UTF8_ERR_INVALID_ARG);
-  return cuda_status(launch_locate_batch(data, offsets, count, out, d->cfg, d->sm_count, stream));
+  return cuda_status(launch_locate_batch(data, offsets, count, out, config_of(*d), d->sm_count, stream));
 }
 
 bool utf8_validate_host(const uint8_t* host_data, size_t len, cudaStream_t stream) {
@@ -239,7 +248,8 @@ bool utf8_validate_host(const uint8_t* host_data, size_t len, cudaStream_t strea
   if (!d) return false;
   std::lock_guard<std::mutex> lock(d->stage_mu);
   cudaError_t e = cudaSuccess;
-  const uint64_t tb = tile_bytes(d->cfg);
+  const LaunchCfg cfg = config_of(*d);
+  const uint64_t tb = tile_bytes(cfg);
   const uint64_t chunk = env_size("UTF8GPU_STAGE_CHUNK", kStageChunk, tb);
   const uint64_t max_window = env_size("UTF8GPU_STAGE_WINDOW", kStageWindow, chunk);
   // staging buffer: one halo tile + a window of whole chunks
@@ -293,7 +303,7 @@ bool utf8_validate_host(const uint8_t* host_data, size_t len, cudaStream_t strea
       const uint64_t t_begin = first_tile + (c0 / tb);
       const uint64_t t_end = last_chunk ? ~uint64_t(0) : done / tb;
       if (e == cudaSuccess)
-        e = launch_validate_tiles(span_data, span_n, t_begin, t_end, result, d->cfg, d->sm_count,
+        e = launch_validate_tiles(span_data, span_n, t_begin, t_end, result, cfg, d->sm_count,
                                   stream);
     }
   }
@@ -316,7 +326,7 @@ int utf8_copy_validate(uint8_t* dst, const uint8_t* src, size_t len, uint8_t* ou
   if (!is_device_memory(out_valid) || (len > 0 && (!is_device_memory(dst) || !is_device_memory(src))))
     return set_status(UTF8_ERR_INVALID_ARG);
   return cuda_status(
-      launch_copy_validate(dst, src, len, out_valid, dev->cfg, dev->sm_count, stream));
+      launch_copy_validate(dst, src, len, out_valid, config_of(*dev), dev->sm_count, stream));
 }
 
 int utf8_classify_debug(const uint8_t* data, size_t len, uint8_t* out_special,
@@ -365,11 +375,12 @@ int utf8_config_json(char* buf, size_t cap) {
   DeviceState* d = device();
   if (!d) return -1;
   char tmp[256];
+  const LaunchCfg cfg = config_of(*d);
   const int n = snprintf(tmp, sizeof tmp,
                          "{\"rows\": %d, \"blocks_per_sm\": %d, \"batch_rows\": %d, "
                          "\"batch_blocks_per_sm\": %d, \"sm_count\": %d}",
-                         d->cfg.rows, d->cfg.blocks_per_sm, d->cfg.batch_rows,
-                         d->cfg.batch_blocks_per_sm, d->sm_count);
+                         cfg.rows, cfg.blocks_per_sm, cfg.batch_rows, cfg.batch_blocks_per_sm,
+                         d->sm_count);
   if (buf != nullptr && cap > 0) {
     strncpy(buf, tmp, cap - 1);
     buf[cap - 1] = 0;
