@@ -108,6 +108,13 @@ LaunchCfg config_of(DeviceState& d) {
   return d.cfg;
 }
 
+int cuda_status(cudaError_t e) { return set_status(e == cudaSuccess ? UTF8_OK : UTF8_ERR_CUDA); }
+
+}  // namespace
+
+// Status setter for entry points defined in other files.
+int set_thread_status(int status) { return set_status(status); }
+
 bool is_device_memory(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -116,13 +123,6 @@ bool is_device_memory(const void* p) {
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
-
-int cuda_status(cudaError_t e) { return set_status(e == cudaSuccess ? UTF8_OK : UTF8_ERR_CUDA); }
-
-}  // namespace
-
-// Status setter for entry points defined in other files.
-int set_thread_status(int status) { return set_status(status); }
 
 LaunchCfg current_config() {
   DeviceState* d = device();

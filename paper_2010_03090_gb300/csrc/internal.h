@@ -9,6 +9,10 @@ namespace utf8gpu {
 
 constexpr int kBlockThreads = 256;
 
+// Host helpers of the C-ABI layer (api.cu).
+int set_thread_status(int status);      // sets the calling thread's utf8_last_error()
+bool is_device_memory(const void* p);   // device or managed memory (cudaPointerGetAttributes)
+
 // Launch configuration (picked by the autotuner, or the defaults below).
 struct LaunchCfg {
   int rows = 8;           // tile rows per warp (tile = rows * 512 bytes): 2, 4 or 8

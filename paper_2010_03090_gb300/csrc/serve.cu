@@ -26,9 +26,6 @@
 #include "tune.h"
 #include "utf8gpu.h"
 
-namespace utf8gpu {
-int set_thread_status(int status);  // api.cu
-}
 
 using namespace utf8gpu;
 
@@ -227,15 +224,6 @@ void destroy_slots(utf8_server* s) {
     cudaFree(slot.d_flags);
   }
   s->slots.clear();
-}
-
-bool is_device_memory(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace

@@ -160,23 +160,9 @@ cudaError_t launch_chunk(const uint8_t* data, uint64_t n, uint32_t prefix,
 
 #include "utf8gpu.h"
 
-namespace utf8gpu {
-int set_thread_status(int status);  // api.cu
-int current_sm_count();             // api.cu
-}  // namespace utf8gpu
-
 using namespace utf8gpu;
 
 namespace {
-
-bool device_ptr(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 int status_of(cudaError_t e) {
   if (e != cudaSuccess) cudaGetLastError();
@@ -199,7 +185,7 @@ int utf8_validate_chunk(const uint8_t* data, size_t len, uint32_t prefix, int pr
                         int final_chunk, uint8_t* out_valid, cudaStream_t stream) {
   if (out_valid == nullptr || (data == nullptr && len > 0) || prefix_len < 0 || prefix_len > 3)
     return set_thread_status(UTF8_ERR_INVALID_ARG);
-  if (!device_ptr(out_valid) || (len > 0 && !device_ptr(data)))
+  if (!is_device_memory(out_valid) || (len > 0 && !is_device_memory(data)))
     return set_thread_status(UTF8_ERR_INVALID_ARG);
   const int sms = current_sm_count();
   if (sms <= 0) return set_thread_status(UTF8_ERR_CUDA);
@@ -239,7 +225,7 @@ int utf8_stream_reset(utf8_stream* s, cudaStream_t stream) {
 int utf8_stream_update(utf8_stream* s, const uint8_t* chunk, size_t len, cudaStream_t stream) {
   if (!s || (chunk == nullptr && len > 0)) return set_thread_status(UTF8_ERR_INVALID_ARG);
   if (len == 0) return set_thread_status(UTF8_OK);
-  if (!device_ptr(chunk)) return set_thread_status(UTF8_ERR_INVALID_ARG);
+  if (!is_device_memory(chunk)) return set_thread_status(UTF8_ERR_INVALID_ARG);
   const uint8_t* tail_in = s->dev + 4 * (s->chunks & 1);
   uint8_t* tail_out = s->dev + 4 * ((s->chunks + 1) & 1);
   const cudaError_t e =
@@ -250,7 +236,7 @@ int utf8_stream_update(utf8_stream* s, const uint8_t* chunk, size_t len, cudaStr
 
 int utf8_stream_finish(utf8_stream* s, uint8_t* out_valid, cudaStream_t stream) {
   if (!s || out_valid == nullptr) return set_thread_status(UTF8_ERR_INVALID_ARG);
-  if (!device_ptr(out_valid)) return set_thread_status(UTF8_ERR_INVALID_ARG);
+  if (!is_device_memory(out_valid)) return set_thread_status(UTF8_ERR_INVALID_ARG);
   // end of stream: an empty final chunk after the current tail
   const uint8_t* tail_in = s->dev + 4 * (s->chunks & 1);
   cudaError_t e = launch_chunk(s->dev + 12, 0, 0, tail_in, 1, s->dev + 8, nullptr, s->sm_count,
