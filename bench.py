@@ -589,6 +589,26 @@ def bench_batch(u, torch, stream, peak: float, sample: int = 20000,
         _, rule = u.error_info_fields(info)
         res["locate"] = {"ms": round(lms, 4), "gbs": round(data.size / (lms / 1e3) / 1e9, 1),
                          "rules_match_flags": bool(torch.equal(rule == 0, out == 1))}
+    # the heavy-skew batch: 20k Pareto(1.1) lengths, 8 B .. 256 MiB, about 4 GiB
+    del d, o, out
+    data, offsets, bad = synth.workload_heavy_skew()
+    d = torch.from_numpy(data).cuda()
+    o = torch.from_numpy(offsets).cuda()
+    out = torch.empty(offsets.size - 1, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            u.utf8_validate_batch(d, o, out, stream=stream)
+        a.record(stream)
+        for _ in range(5):
+            u.utf8_validate_batch(d, o, out, stream=stream)
+        b.record(stream)
+    stream.synchronize()
+    hms = a.elapsed_time(b) / 5
+    flagged = set(np.nonzero(out.cpu().numpy() == 0)[0].tolist())
+    res["heavy_skew"] = {"strings": int(offsets.size - 1), "bytes": int(data.size),
+                         "longest_string": int(np.diff(offsets).max()),
+                         "ms": round(hms, 3), "gbs": round(data.size / (hms / 1e3) / 1e9, 1),
+                         "corrupted_flagged": flagged == set(bad.tolist())}
     return res
 
 
