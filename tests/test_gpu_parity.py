@@ -354,3 +354,36 @@ def test_autotune_and_cache(tmp_path):
     assert u.utf8_validate(dev(base))
     base[12345] = 0xBF
     assert not u.utf8_validate(dev(base))
+
+
+def test_tiny_batches_around_group_sizes():
+    """Batches of 1 .. 97 strings (boundary groups of 32 are checked
+    together), with empty strings, all-empty batches and errors in the first
+    and last strings; flags and error locations against the oracle."""
+    rng = np.random.default_rng(23)
+    for count in (1, 2, 3, 31, 32, 33, 63, 64, 65, 96, 97):
+        for trial in range(3):
+            lens = rng.integers(0, 40, count)
+            if trial == 1:
+                lens[rng.random(count) < 0.5] = 0
+            if trial == 2 and count > 2:
+                lens[:] = 0
+                lens[count // 2] = 7
+            strings = [synth.fill(int(n), synth.UNIFORM, seed=count * 10 + trial * 1000 + i)
+                       for i, n in enumerate(lens)]
+            if strings[0].size:
+                strings[0][0] = 0x80
+            if strings[-1].size:
+                strings[-1][-1] = 0xE2
+            offsets = synth.offsets_of([s.size for s in strings])
+            data = np.concatenate(strings) if offsets[-1] else np.zeros(0, np.uint8)
+            for shift in (0, 5):
+                shifted = np.concatenate([np.full(shift, 0x41, np.uint8), data])
+                got = batch_flags(shifted, offsets + shift)
+                assert np.array_equal(got, oracle.valid_batch(data, offsets)), (count, trial, shift)
+                d = dev(shifted) if shifted.size else torch.zeros(16, dtype=torch.uint8, device="cuda")
+                pos, rule = u.error_info_fields(u.utf8_locate_errors_batch(
+                    d, torch.from_numpy(offsets + shift).cuda()))
+                want_pos, want_rule = oracle.locate_batch(data, offsets)
+                assert np.array_equal(pos.cpu().numpy(), want_pos), (count, trial, shift)
+                assert np.array_equal(rule.cpu().numpy(), want_rule), (count, trial, shift)
