@@ -44,6 +44,8 @@ struct SegmentDesc {
 uint64_t segment_tiles(const uint8_t* data, uint64_t len, const LaunchCfg& cfg);
 
 // tile_prefix: device int64[count + 1], exclusive prefix of segment_tiles.
+// out_valid[0 .. count) must hold 1 before the launch; the kernel clears the
+// flags of invalid segments (it may be host memory mapped into the device).
 cudaError_t launch_segments(const SegmentDesc* segs, const int64_t* tile_prefix, int64_t count,
                             uint64_t total_tiles, uint8_t* out_valid, const LaunchCfg& cfg,
                             int sm_count, cudaStream_t st);

@@ -59,8 +59,6 @@ cudaError_t launch_segments(const SegmentDesc* segs, const int64_t* tile_prefix,
                             uint64_t total_tiles, uint8_t* out_valid, const LaunchCfg& cfg,
                             int sm_count, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(out_valid, 1, (size_t)count, st);
-  if (e != cudaSuccess) return e;
   const uint64_t warps_per_block = kBlockThreads / kLanes;
   uint64_t grid = (uint64_t)sm_count * (uint64_t)cfg.blocks_per_sm;
   const uint64_t need = (total_tiles + warps_per_block - 1) / warps_per_block;

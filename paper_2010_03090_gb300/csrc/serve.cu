@@ -55,18 +55,22 @@ struct Result {
   int64_t latency_ns = 0;
 };
 
+// A batch slot.  The batch's descriptors (n SegmentDesc, then the n + 1
+// entries of the tile prefix) go to the device in one copy; the flags live in
+// pinned host memory mapped into the device, set to 1 by the host before the
+// launch and cleared by the kernel, so no copy brings them back.
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  SegmentDesc* h_segs = nullptr;  // pinned
-  int64_t* h_prefix = nullptr;
-  uint8_t* h_flags = nullptr;
-  SegmentDesc* d_segs = nullptr;  // device
-  int64_t* d_prefix = nullptr;
-  uint8_t* d_flags = nullptr;
+  uint8_t* h_desc = nullptr;    // pinned
+  uint8_t* d_desc = nullptr;    // device
+  uint8_t* h_flags = nullptr;   // pinned, mapped
+  uint8_t* dm_flags = nullptr;  // its device address
   std::vector<Request> reqs;
   bool busy = false;
 };
+
+size_t desc_bytes(size_t n) { return n * sizeof(SegmentDesc) + (n + 1) * sizeof(int64_t); }
 
 }  // namespace
 
@@ -104,24 +108,24 @@ void admit_waiting(utf8_server* s) {  // caller holds mu
 
 cudaError_t launch_slot(utf8_server* s, Slot& slot) {
   const int64_t n = (int64_t)slot.reqs.size();
+  SegmentDesc* h_segs = reinterpret_cast<SegmentDesc*>(slot.h_desc);
+  int64_t* h_prefix = reinterpret_cast<int64_t*>(slot.h_desc + n * sizeof(SegmentDesc));
   int64_t tiles = 0;
   for (int64_t k = 0; k < n; ++k) {
-    slot.h_segs[k].data = slot.reqs[k].data;
-    slot.h_segs[k].len = slot.reqs[k].len;
-    slot.h_prefix[k] = tiles;
+    h_segs[k].data = slot.reqs[k].data;
+    h_segs[k].len = slot.reqs[k].len;
+    h_prefix[k] = tiles;
     tiles += (int64_t)segment_tiles(slot.reqs[k].data, slot.reqs[k].len, s->launch);
+    slot.h_flags[k] = 1;
   }
-  slot.h_prefix[n] = tiles;
-  cudaError_t e = cudaMemcpyAsync(slot.d_segs, slot.h_segs, n * sizeof(SegmentDesc),
+  h_prefix[n] = tiles;
+  std::atomic_thread_fence(std::memory_order_release);
+  cudaError_t e = cudaMemcpyAsync(slot.d_desc, slot.h_desc, desc_bytes((size_t)n),
                                   cudaMemcpyHostToDevice, slot.stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(slot.d_prefix, slot.h_prefix, (n + 1) * sizeof(int64_t),
-                        cudaMemcpyHostToDevice, slot.stream);
-  if (e == cudaSuccess)
-    e = launch_segments(slot.d_segs, slot.d_prefix, n, (uint64_t)tiles, slot.d_flags, s->launch,
-                        s->sm_count, slot.stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(slot.h_flags, slot.d_flags, n, cudaMemcpyDeviceToHost, slot.stream);
+    e = launch_segments(reinterpret_cast<const SegmentDesc*>(slot.d_desc),
+                        reinterpret_cast<const int64_t*>(slot.d_desc + n * sizeof(SegmentDesc)), n,
+                        (uint64_t)tiles, slot.dm_flags, s->launch, s->sm_count, slot.stream);
   if (e == cudaSuccess) e = cudaEventRecord(slot.done, slot.stream);
   return e;
 }
@@ -225,12 +229,9 @@ void destroy_slots(utf8_server* s) {
   for (Slot& slot : s->slots) {
     if (slot.done) cudaEventDestroy(slot.done);
     if (slot.stream) cudaStreamDestroy(slot.stream);
-    cudaFreeHost(slot.h_segs);
-    cudaFreeHost(slot.h_prefix);
+    cudaFreeHost(slot.h_desc);
     cudaFreeHost(slot.h_flags);
-    cudaFree(slot.d_segs);
-    cudaFree(slot.d_prefix);
-    cudaFree(slot.d_flags);
+    cudaFree(slot.d_desc);
   }
   s->slots.clear();
 }
@@ -273,12 +274,11 @@ utf8_server* utf8_server_create(const utf8_server_config* cfg) {
     const size_t n = c.max_batch;
     e = cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaHostAlloc(&slot.h_segs, n * sizeof(SegmentDesc), 0);
-    if (e == cudaSuccess) e = cudaHostAlloc(&slot.h_prefix, (n + 1) * sizeof(int64_t), 0);
-    if (e == cudaSuccess) e = cudaHostAlloc(&slot.h_flags, n, 0);
-    if (e == cudaSuccess) e = cudaMalloc(&slot.d_segs, n * sizeof(SegmentDesc));
-    if (e == cudaSuccess) e = cudaMalloc(&slot.d_prefix, (n + 1) * sizeof(int64_t));
-    if (e == cudaSuccess) e = cudaMalloc(&slot.d_flags, n);
+    if (e == cudaSuccess) e = cudaHostAlloc(&slot.h_desc, desc_bytes(n), 0);
+    if (e == cudaSuccess) e = cudaMalloc(&slot.d_desc, desc_bytes(n));
+    if (e == cudaSuccess) e = cudaHostAlloc(&slot.h_flags, n, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&slot.dm_flags),
+                                                       slot.h_flags, 0);
     slot.reqs.reserve(n);
   }
   if (e != cudaSuccess) {
