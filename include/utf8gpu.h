@@ -26,10 +26,10 @@
  *     thread's last call is also kept for utf8_last_error(), which is the only
  *     way to see it for utf8_validate(), whose result is a bool.
  *   - The library allocates small per-device work areas on a device's first
- *     call (a ring of result bytes and its pinned host mirror; the staging
- *     buffer of utf8_validate_host on its first use); make that first call
- *     before capturing any stream into a CUDA graph.  It never frees caller
- *     memory.  Entry points are thread safe.
+ *     call (a ring of result bytes in pinned host memory mapped into the
+ *     device; the staging buffer of utf8_validate_host on its first use); make
+ *     that first call before capturing any stream into a CUDA graph.  It never
+ *     frees caller memory.  Entry points are thread safe.
  */
 #ifndef UTF8GPU_H
 #define UTF8GPU_H

@@ -1,10 +1,9 @@
 // The C-ABI of libutf8gpu.so (declared in include/utf8gpu.h).
 //
 // Host-side runtime: per-device state (SM count, launch configuration, a ring
-// of result bytes with a pinned host mirror, the staging buffer and copy
-// stream of the host-memory path), argument checks and status codes.  All
-// validation work runs in the kernels of validate.cu and batch.cu; there is
-// no CPU path.
+// of result bytes in pinned host memory mapped into the device, the staging
+// buffer and copy stream of the host-memory path), argument checks and status
+// codes.  All validation work runs in the kernels; there is no CPU path.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -52,8 +51,11 @@ struct DeviceState {
   int sm_count = 0;
   std::mutex cfg_mu;  // guards cfg: the autotuner and cache loads replace it
   LaunchCfg cfg;
-  uint8_t* d_results = nullptr;  // kResultSlots result bytes
-  uint8_t* h_results = nullptr;  // pinned mirror
+  // kResultSlots result bytes of the synchronous calls, in pinned host memory
+  // mapped into the device: the host sets a slot to 1, the kernels clear it
+  // on an error, the host reads it after synchronising (no copies)
+  uint8_t* h_results = nullptr;
+  uint8_t* dm_results = nullptr;  // the device address of h_results
   std::atomic<uint32_t> next_slot{0};
   utf8_error_info* d_info = nullptr;  // kInfoSlots error locations
   utf8_error_info* h_info = nullptr;  // pinned mirror
@@ -76,9 +78,10 @@ void init_device(DeviceState& d, int dev) {
     d.sm_count = prop.multiProcessorCount;
     d.cfg = tuned_config(prop.name, prop.multiProcessorCount);
     clamp_to_occupancy(d.cfg);
-    e = cudaMalloc(&d.d_results, kResultSlots);
+    e = cudaHostAlloc(&d.h_results, kResultSlots, cudaHostAllocMapped);
   }
-  if (e == cudaSuccess) e = cudaHostAlloc(&d.h_results, kResultSlots, cudaHostAllocDefault);
+  if (e == cudaSuccess)
+    e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&d.dm_results), d.h_results, 0);
   if (e == cudaSuccess) e = cudaMalloc(&d.d_info, kInfoSlots * sizeof(utf8_error_info));
   if (e == cudaSuccess)
     e = cudaHostAlloc(&d.h_info, kInfoSlots * sizeof(utf8_error_info), cudaHostAllocDefault);
@@ -157,14 +160,15 @@ bool utf8_validate(const uint8_t* data, size_t len, cudaStream_t stream) {
   if (!d) return false;
   if (!is_device_memory(data)) return set_status(UTF8_ERR_INVALID_ARG), false;
   const uint32_t slot = d->next_slot.fetch_add(1) % kResultSlots;
-  cudaError_t e = launch_validate(data, len, d->d_results + slot, config_of(*d), d->sm_count, stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d->h_results + slot, d->d_results + slot, 1, cudaMemcpyDeviceToHost,
-                        stream);
+  volatile uint8_t* h = d->h_results + slot;
+  *h = 1;
+  std::atomic_thread_fence(std::memory_order_release);
+  cudaError_t e = launch_validate_tiles(data, len, 0, ~uint64_t(0), d->dm_results + slot,
+                                        config_of(*d), d->sm_count, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return cuda_status(e), false;
   set_status(UTF8_OK);
-  return d->h_results[slot] == 1;
+  return *h == 1;
 }
 
 int utf8_validate_async(const uint8_t* data, size_t len, uint8_t* out_valid,
@@ -271,8 +275,10 @@ bool utf8_validate_host(const uint8_t* host_data, size_t len, cudaStream_t strea
     if (e != cudaSuccess) return cuda_status(e), false;
   }
   const uint32_t slot = d->next_slot.fetch_add(1) % kResultSlots;
-  uint8_t* result = d->d_results + slot;
-  e = cudaMemsetAsync(result, 1, 1, stream);
+  uint8_t* result = d->dm_results + slot;
+  volatile uint8_t* h = d->h_results + slot;
+  *h = 1;
+  std::atomic_thread_fence(std::memory_order_release);
   // Window k holds host bytes [k*window, ...) at d_stage + tb, preceded by the
   // tile of bytes before it (the halo) for k >= 1.
   uint64_t chunk_id = 0;
@@ -307,12 +313,10 @@ bool utf8_validate_host(const uint8_t* host_data, size_t len, cudaStream_t strea
                                   stream);
     }
   }
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d->h_results + slot, result, 1, cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return cuda_status(e), false;
   set_status(UTF8_OK);
-  return d->h_results[slot] == 1;
+  return *h == 1;
 }
 
 int utf8_copy_validate(uint8_t* dst, const uint8_t* src, size_t len, uint8_t* out_valid,
