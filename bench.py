@@ -232,7 +232,30 @@ def oracle_baseline(bufs, names, seconds: float) -> dict:
             "sample": f"last {per >> 20} MiB (from a character start) of each of the "
                       f"{len(bufs)} buffers, {total / 1e9:.2f} GB, {dt:.1f} s, one thread",
             "flags": dict(zip(names, got)),
-            "all_cores": oracle_all_cores(samples, names, got)}
+            "all_cores": oracle_all_cores(samples, names, got),
+            "cpu_lookup": cpu_lookup_baseline(samples, got)}
+
+
+def cpu_lookup_baseline(samples, oracle_flags) -> dict:
+    """The paper's `lookup` on the host CPU (16-byte vectors: tbl/ext on Arm)
+    over the same samples, one thread and every core: context for the GPU
+    figures, like the oracle, not a target."""
+    import cpu_lookup
+    cpu_lookup.valid(samples[0][:1 << 20])  # build and warm the library
+    t = time.perf_counter()
+    got = [cpu_lookup.valid(x) for x in samples]
+    dt = time.perf_counter() - t
+    total = sum(x.size for x in samples)
+    threads = max(len(os.sched_getaffinity(0)), 1)
+    cuts = [split_at_char_starts(x, 4 * threads) for x in samples]
+    t = time.perf_counter()
+    got_all = [bool(cpu_lookup.valid_batch(x, c, threads=threads).all()) for x, c in zip(samples, cuts)]
+    dt_all = time.perf_counter() - t
+    return {"value": round(total / dt / 1e9, 3), "unit": "GB/s", "cores": 1,
+            "all_cores": {"value": round(total / dt_all / 1e9, 3), "cores": threads},
+            "kind": "the paper's lookup, 16-byte vector lookups on the host CPU",
+            "sample": f"the same {total / 1e9:.2f} GB as the oracle",
+            "flags_match_oracle": got == list(oracle_flags) == got_all}
 
 
 def split_at_char_starts(buf: np.ndarray, pieces: int) -> np.ndarray:
