@@ -257,8 +257,10 @@ __global__ void __launch_bounds__(kBlockThreads)
       const int64_t oj = g_off;
       int64_t o_prev = __shfl_up_sync(kFull, oj, 1);
       int64_t o_next = __shfl_down_sync(kFull, oj, 1);
+      const int64_t after_group = __shfl_sync(kFull, g_nxt, 0);  // offsets[group_last + 1]
       if (lane == 0) o_prev = prev_off;
-      if (act && j == group_last && j < count) o_next = offsets[j + 1];
+      if (act && j == group_last && j < count)
+        o_next = group_last + 1 < b1 ? after_group : offsets[j + 1];
       if (act) {
         const int64_t lo = j >= 1 ? o_prev : oj;
         const int64_t hi = j < count ? o_next : oj;
