@@ -88,6 +88,17 @@ int utf8_validate_batch(const uint8_t* data, const int64_t* offsets, int64_t cou
                         uint8_t* out_valid, cudaStream_t stream);
 
 /*
+ * Checks batch offsets on the device (one pass): offsets[0] >= 0 and
+ * offsets[0 .. count] non-decreasing.  Synchronises `stream`; returns
+ * UTF8_OK or UTF8_ERR_INVALID_ARG (also for a null or host pointer).
+ * With the environment variable UTF8GPU_CHECK_OFFSETS=1 (read once per
+ * process) utf8_validate_batch and utf8_locate_errors_batch run this check
+ * first and return its error instead of launching: an opt-in debug mode that
+ * makes those calls synchronous.
+ */
+int utf8_check_offsets(const int64_t* offsets, int64_t count, cudaStream_t stream);
+
+/*
  * Where validation fails (the paper's validators answer valid / invalid;
  * these report where and why, from the same `lookup` pass).
  *

@@ -34,6 +34,7 @@ from ._lib import (  # noqa: F401
     utf8_locate_error,
     utf8_locate_error_async,
     utf8_locate_errors_batch,
+    utf8_check_offsets,
     error_info_fields,
     ErrorInfo,
     RULES,

@@ -19,6 +19,7 @@ EXPORTS = (
     "utf8_server_destroy", "utf8_validate_chunk", "utf8_stream_create", "utf8_stream_reset",
     "utf8_stream_update", "utf8_stream_finish", "utf8_stream_destroy", "utf8_copy_validate",
     "utf8_locate_error", "utf8_locate_error_async", "utf8_locate_errors_batch",
+    "utf8_check_offsets",
 )
 
 # Section 3's rules a-f as the library numbers them (enum utf8_rule).
@@ -95,6 +96,8 @@ def lib() -> ctypes.CDLL:
             L.utf8_locate_error_async.restype = i32
             L.utf8_locate_errors_batch.argtypes = [vp, vp, i64, vp, vp]
             L.utf8_locate_errors_batch.restype = i32
+            L.utf8_check_offsets.argtypes = [vp, i64, vp]
+            L.utf8_check_offsets.restype = i32
             _lib = L
     return _lib
 
@@ -228,6 +231,15 @@ def error_info_fields(out):
     import torch
     t = out.reshape(-1, 2)
     return t[:, 0], (t[:, 1] & 0xFFFFFFFF).to(torch.int32)  # rule: low half, little-endian
+
+
+def utf8_check_offsets(offsets, stream=None) -> None:
+    """Raises Utf8Error (status 1) unless offsets[0] >= 0 and the int64 CUDA
+    tensor is non-decreasing (checked on the device; synchronises)."""
+    q, m = _dev(offsets, "int64", "offsets")
+    if m < 1:
+        raise ValueError("offsets needs at least one entry")
+    _check(lib().utf8_check_offsets(q, m - 1, _stream(stream)), "utf8_check_offsets")
 
 
 def utf8_validate_host(host, stream=None) -> bool:

@@ -113,6 +113,28 @@ LaunchCfg config_of(DeviceState& d) {
 
 int cuda_status(cudaError_t e) { return set_status(e == cudaSuccess ? UTF8_OK : UTF8_ERR_CUDA); }
 
+// UTF8GPU_CHECK_OFFSETS=1: the batch entry points check the offsets first.
+bool offsets_debug_mode() {
+  static const bool on = [] {
+    const char* v = getenv("UTF8GPU_CHECK_OFFSETS");
+    return v != nullptr && v[0] != 0 && v[0] != '0';
+  }();
+  return on;
+}
+
+// Runs the offsets check on `stream` and waits for it: UTF8_OK when the
+// offsets are well-formed, UTF8_ERR_INVALID_ARG when not.
+int check_offsets(DeviceState* d, const int64_t* offsets, int64_t count, cudaStream_t stream) {
+  const uint32_t slot = d->next_slot.fetch_add(1) % kResultSlots;
+  volatile uint8_t* h = d->h_results + slot;
+  *h = 1;
+  std::atomic_thread_fence(std::memory_order_release);
+  cudaError_t e = launch_check_offsets(offsets, count, d->dm_results + slot, d->sm_count, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  return set_status(*h == 1 ? UTF8_OK : UTF8_ERR_INVALID_ARG);
+}
+
 }  // namespace
 
 // Status setter for entry points defined in other files.
@@ -193,7 +215,17 @@ int utf8_validate_batch(const uint8_t* data, const int64_t* offsets, int64_t cou
   if (!d) return UTF8_ERR_CUDA;
   if (!is_device_memory(data) || !is_device_memory(offsets) || !is_device_memory(out_valid))
     return set_status(UTF8_ERR_INVALID_ARG);
+  if (offsets_debug_mode() && check_offsets(d, offsets, count, stream) != UTF8_OK)
+    return utf8_last_error();
   return cuda_status(launch_batch(data, offsets, count, out_valid, config_of(*d), d->sm_count, stream));
+}
+
+int utf8_check_offsets(const int64_t* offsets, int64_t count, cudaStream_t stream) {
+  if (count < 0 || offsets == nullptr) return set_status(UTF8_ERR_INVALID_ARG);
+  DeviceState* d = device();
+  if (!d) return UTF8_ERR_CUDA;
+  if (!is_device_memory(offsets)) return set_status(UTF8_ERR_INVALID_ARG);
+  return check_offsets(d, offsets, count, stream);
 }
 
 int utf8_locate_error_async(const uint8_t* data, size_t len, utf8_error_info* out,
@@ -242,6 +274,8 @@ int utf8_locate_errors_batch(const uint8_t* data, const int64_t* offsets, int64_
   if (!d) return UTF8_ERR_CUDA;
   if (!is_device_memory(data) || !is_device_memory(offsets) || !is_device_memory(out))
     return set_status(UTF8_ERR_INVALID_ARG);
+  if (offsets_debug_mode() && check_offsets(d, offsets, count, stream) != UTF8_OK)
+    return utf8_last_error();
   return cuda_status(launch_locate_batch(data, offsets, count, out, config_of(*d), d->sm_count, stream));
 }
 

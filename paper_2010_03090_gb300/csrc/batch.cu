@@ -327,6 +327,33 @@ cudaError_t launch_batch_first_errors(const uint8_t* data, const int64_t* offset
 
 namespace utf8gpu {
 
+// Offsets well-formed: offsets[0] >= 0 and non-decreasing; clears *out_ok
+// otherwise (the caller sets it to 1).
+__global__ void check_offsets_kernel(const int64_t* __restrict__ offsets, int64_t count,
+                                     uint8_t* out_ok) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= count; i += stride) {
+    const int64_t o = offsets[i];
+    if (i == 0 && o < 0) bad = true;
+    if (i < count && o > offsets[i + 1]) bad = true;
+  }
+  if (bad) *out_ok = 0;
+}
+
+cudaError_t launch_check_offsets(const int64_t* offsets, int64_t count, uint8_t* out_ok,
+                                 int sm_count, cudaStream_t st) {
+  const int64_t blocks = (count + 1 + 255) / 256;
+  const int64_t cap = (int64_t)sm_count * 8;
+  check_offsets_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, st>>>(offsets, count,
+                                                                               out_ok);
+  return cudaGetLastError();
+}
+
+}  // namespace utf8gpu
+
+namespace utf8gpu {
+
 int batch_blocks_per_sm(int rows) {
   int n = 0;
   cudaError_t e;

@@ -66,6 +66,11 @@ int copy_blocks_per_sm(int rows, int wanted);
 cudaError_t launch_batch(const uint8_t* data, const int64_t* offsets, int64_t count,
                          uint8_t* out_valid, const LaunchCfg& cfg, int sm_count, cudaStream_t st);
 
+// Clears *out_ok unless offsets[0] >= 0 and offsets[0 .. count] is
+// non-decreasing (batch.cu).
+cudaError_t launch_check_offsets(const int64_t* offsets, int64_t count, uint8_t* out_ok,
+                                 int sm_count, cudaStream_t st);
+
 // Error location (locate.cu): *out / out[count] are set to all ones, marked
 // with the first erroneous position(s), then settled into utf8_error_info.
 cudaError_t launch_locate(const uint8_t* data, uint64_t n, utf8_error_info* out,

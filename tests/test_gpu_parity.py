@@ -387,3 +387,46 @@ def test_tiny_batches_around_group_sizes():
                 want_pos, want_rule = oracle.locate_batch(data, offsets)
                 assert np.array_equal(pos.cpu().numpy(), want_pos), (count, trial, shift)
                 assert np.array_equal(rule.cpu().numpy(), want_rule), (count, trial, shift)
+
+
+def test_check_offsets():
+    ok = [[0, 3, 3, 10], [5], [0, 0, 0]]
+    bad = [[0, 5, 3, 10], [-1, 2, 3], [0, 1, 2, 1]]
+    for o in ok:
+        u.utf8_check_offsets(torch.tensor(o, dtype=torch.int64, device="cuda"))
+    for o in bad:
+        with pytest.raises(u.Utf8Error) as e:
+            u.utf8_check_offsets(torch.tensor(o, dtype=torch.int64, device="cuda"))
+        assert e.value.code == 1
+    big = torch.arange(0, 3_000_001, dtype=torch.int64, device="cuda")
+    u.utf8_check_offsets(big)
+    big[-1] = 17  # one decreasing pair at the very end (grid-stride coverage)
+    with pytest.raises(u.Utf8Error):
+        u.utf8_check_offsets(big)
+
+
+def test_offsets_debug_mode_rejects_before_launch():
+    """UTF8GPU_CHECK_OFFSETS=1 (read once per process, so in a child):
+    the batch entry points refuse malformed offsets with status 1.  The
+    offsets stay inside the data, so nothing out of range would be read even
+    without the check."""
+    import subprocess
+    import sys
+    code = (
+        "import torch, paper_2010_03090_gb300 as u\n"
+        "d = torch.zeros(16, dtype=torch.uint8, device='cuda')\n"
+        "good = torch.tensor([0, 3, 3, 10], dtype=torch.int64, device='cuda')\n"
+        "print(u.utf8_validate_batch(d, good).tolist())\n"
+        "bad = torch.tensor([0, 5, 3, 10], dtype=torch.int64, device='cuda')\n"
+        "for f in (u.utf8_validate_batch, u.utf8_locate_errors_batch):\n"
+        "    try:\n"
+        "        f(d, bad)\n"
+        "        print('launched')\n"
+        "    except u.Utf8Error as e:\n"
+        "        print('rejected', e.code)\n")
+    env = dict(os.environ, UTF8GPU_CHECK_OFFSETS="1")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.split("\n")[:3] == ["[1, 1, 1]", "rejected 1", "rejected 1"], r.stdout
