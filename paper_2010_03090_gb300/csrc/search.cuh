@@ -7,7 +7,7 @@
 namespace utf8gpu {
 
 // Range [lo, hi]: the answer (first index j in [lo, hi) with a[j] >= target,
-// or hi if there is none) lies in it.  One round probes j_k = lo + k * step
+// or hi if there is none) lies in it.  One step probes j_k = lo + k * step
 // (k = 0..31; a probe at or past hi counts as true) and narrows the range from
 // the probe mask (bit k = probe k true).
 struct LbRange {
