@@ -50,3 +50,23 @@ def test_library_links_no_shared_runtime():
     out = subprocess.run(["readelf", "-d", u.lib_path()], capture_output=True, text=True).stdout
     assert "libcudart" not in out  # static CUDA runtime: only the driver is needed
     assert "libtorch" not in out
+
+
+def _build_c_example(out_dir):
+    """Compiles tests/host/c_abi_example.c as C99 against the header and links
+    it with the library (no GPU needed to build)."""
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    exe = os.path.join(str(out_dir), "c_abi_example")
+    lib_dir = os.path.dirname(u.lib_path())
+    u.lib()
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I",
+                    os.path.join(ROOT, "include"), "-I", os.path.join(cuda, "include"),
+                    os.path.join(ROOT, "tests", "host", "c_abi_example.c"), "-o", exe,
+                    "-L", lib_dir, "-lutf8gpu", f"-Wl,-rpath,{lib_dir}",
+                    "-L", os.path.join(cuda, "lib64"), "-lcudart", f"-Wl,-rpath,{os.path.join(cuda, 'lib64')}"],
+                   check=True)
+    return exe
+
+
+def test_c_program_compiles_against_the_header(tmp_path):
+    assert os.path.exists(_build_c_example(tmp_path))
