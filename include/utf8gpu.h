@@ -80,9 +80,11 @@ int utf8_validate_async(const uint8_t* data, size_t len, uint8_t* out_valid,
  * its neighbours' bytes.  out_valid: device uint8[count], 1 = valid, 0 =
  * invalid.  data must be non-null (and device memory) even when every string
  * is empty.  Asynchronous on `stream`.  count == 0 is a no-op.  Offsets are not
- * checked on the device; decreasing offsets give unspecified flags (never an
- * out-of-range access beyond [data + offsets[0], data + offsets[count]) is
- * made by a well-formed call).  Returns a status.
+ * checked by default (utf8_check_offsets below, or UTF8GPU_CHECK_OFFSETS=1,
+ * checks them); malformed offsets give unspecified flags, and only a
+ * well-formed call is guaranteed to read nothing outside the aligned 16-byte
+ * granules that hold bytes of [data + offsets[0], data + offsets[count]).
+ * Returns a status.
  */
 int utf8_validate_batch(const uint8_t* data, const int64_t* offsets, int64_t count,
                         uint8_t* out_valid, cudaStream_t stream);
@@ -310,9 +312,11 @@ const char* utf8_error_string(int code);
  * Autotuning of the launch configuration (tile rows per warp and resident
  * CTAs per SM, for the single-buffer and the batch kernel) on synthetic data
  * generated on the current device.
- * flags: 0 = tune only what has no cached entry, 1 = retune everything.
- * The cache is keyed by GPU name and SM count; it can be saved to and loaded
- * from a JSON file.  Return a status.
+ * flags: 0 = use the cached entry of this GPU if there is one (and apply it
+ * to the current device), else tune; 1 = retune.  The cache is keyed by GPU
+ * name and SM count; it can be saved to and loaded from a JSON file.  Loaded
+ * entries apply to devices first used afterwards, and to the current device
+ * on utf8_autotune(0).  Return a status.
  */
 int utf8_autotune(int flags);
 int utf8_tune_cache_load(const char* path);
