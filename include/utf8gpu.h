@@ -90,6 +90,26 @@ int utf8_validate_batch(const uint8_t* data, const int64_t* offsets, int64_t cou
                         uint8_t* out_valid, cudaStream_t stream);
 
 /*
+ * utf8_validate_batch with its arguments in a DEVICE descriptor that the
+ * kernels read when they run (count and pointers are not baked into the
+ * launch), so a CUDA graph that captures this call replays for any batch
+ * written into the descriptor between replays: other pointers, another count.
+ * desc: device memory, read on the stream; its fields follow the rules of
+ * utf8_validate_batch.  Two kernels: one sets the count flags to 1, the batch
+ * pass clears those of invalid strings.  Asynchronous; returns a status
+ * (UTF8_ERR_INVALID_ARG for a null or host desc; the descriptor's contents
+ * are not checked on the host).
+ */
+typedef struct {
+    const uint8_t* data;    /* device */
+    const int64_t* offsets; /* device, count + 1 entries */
+    int64_t count;
+    uint8_t* out_valid;     /* device, count entries */
+} utf8_batch_desc;
+
+int utf8_validate_batch_desc(const utf8_batch_desc* desc, cudaStream_t stream);
+
+/*
  * Checks batch offsets on the device (one pass): offsets[0] >= 0 and
  * offsets[0 .. count] non-decreasing.  Synchronises `stream`; returns
  * UTF8_OK or UTF8_ERR_INVALID_ARG (also for a null or host pointer).

@@ -35,6 +35,8 @@ from ._lib import (  # noqa: F401
     utf8_locate_error_async,
     utf8_locate_errors_batch,
     utf8_check_offsets,
+    utf8_validate_batch_desc,
+    batch_desc_values,
     error_info_fields,
     ErrorInfo,
     RULES,

@@ -19,7 +19,7 @@ EXPORTS = (
     "utf8_server_destroy", "utf8_validate_chunk", "utf8_stream_create", "utf8_stream_reset",
     "utf8_stream_update", "utf8_stream_finish", "utf8_stream_destroy", "utf8_copy_validate",
     "utf8_locate_error", "utf8_locate_error_async", "utf8_locate_errors_batch",
-    "utf8_check_offsets",
+    "utf8_check_offsets", "utf8_validate_batch_desc",
 )
 
 # Section 3's rules a-f as the library numbers them (enum utf8_rule).
@@ -98,6 +98,8 @@ def lib() -> ctypes.CDLL:
             L.utf8_locate_errors_batch.restype = i32
             L.utf8_check_offsets.argtypes = [vp, i64, vp]
             L.utf8_check_offsets.restype = i32
+            L.utf8_validate_batch_desc.argtypes = [vp, vp]
+            L.utf8_validate_batch_desc.restype = i32
             _lib = L
     return _lib
 
@@ -231,6 +233,27 @@ def error_info_fields(out):
     import torch
     t = out.reshape(-1, 2)
     return t[:, 0], (t[:, 1] & 0xFFFFFFFF).to(torch.int32)  # rule: low half, little-endian
+
+
+def batch_desc_values(data, offsets, out_valid) -> list:
+    """The four int64 fields of a utf8_batch_desc (data, offsets, count,
+    out_valid) for CUDA tensors; copy them into a device int64[4] tensor."""
+    p, _ = _dev(data, "uint8", "data")
+    q, m = _dev(offsets, "int64", "offsets")
+    r, k = _dev(out_valid, "uint8", "out_valid")
+    if k < m - 1:
+        raise ValueError("out_valid is too small")
+    return [p, q, m - 1, r]
+
+
+def utf8_validate_batch_desc(desc, stream=None) -> None:
+    """Queues the batch described by `desc`, a device int64[4] tensor holding a
+    utf8_batch_desc (see batch_desc_values); the kernels read it when they run,
+    so a captured graph of this call replays for whatever the tensor holds."""
+    q, m = _dev(desc, "int64", "desc")
+    if m < 4:
+        raise ValueError("desc needs four int64 elements")
+    _check(lib().utf8_validate_batch_desc(q, _stream(stream)), "utf8_validate_batch_desc")
 
 
 def utf8_check_offsets(offsets, stream=None) -> None:

@@ -220,6 +220,14 @@ int utf8_validate_batch(const uint8_t* data, const int64_t* offsets, int64_t cou
   return cuda_status(launch_batch(data, offsets, count, out_valid, config_of(*d), d->sm_count, stream));
 }
 
+int utf8_validate_batch_desc(const utf8_batch_desc* desc, cudaStream_t stream) {
+  if (desc == nullptr) return set_status(UTF8_ERR_INVALID_ARG);
+  DeviceState* d = device();
+  if (!d) return UTF8_ERR_CUDA;
+  if (!is_device_memory(desc)) return set_status(UTF8_ERR_INVALID_ARG);
+  return cuda_status(launch_batch_desc(desc, config_of(*d), d->sm_count, stream));
+}
+
 int utf8_check_offsets(const int64_t* offsets, int64_t count, cudaStream_t stream) {
   if (count < 0 || offsets == nullptr) return set_status(UTF8_ERR_INVALID_ARG);
   DeviceState* d = device();

@@ -91,9 +91,10 @@ __device__ __forceinline__ void charge(uint8_t* out_valid, utf8_error_info* out_
 }
 
 template <int ROWS, bool LOCATE>
-__global__ void __launch_bounds__(kBlockThreads)
-    batch_kernel(const uint8_t* __restrict__ data, const int64_t* __restrict__ offsets,
-                 int64_t count, uint8_t* __restrict__ out_valid, utf8_error_info* out_err) {
+__device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
+                                           const int64_t* __restrict__ offsets, int64_t count,
+                                           uint8_t* __restrict__ out_valid,
+                                           utf8_error_info* out_err) {
   constexpr uint64_t kTileBytes = (uint64_t)kLanes * ROWS * 16;
   // The region [offsets[0], offsets[count]) is read on the device, so the
   // launch needs nothing from the host but the pointers (graph capturable).
@@ -284,6 +285,31 @@ __global__ void __launch_bounds__(kBlockThreads)
   }
 }
 
+template <int ROWS, bool LOCATE>
+__global__ void __launch_bounds__(kBlockThreads)
+    batch_kernel(const uint8_t* __restrict__ data, const int64_t* __restrict__ offsets,
+                 int64_t count, uint8_t* __restrict__ out_valid, utf8_error_info* out_err) {
+  batch_body<ROWS, LOCATE>(data, offsets, count, out_valid, out_err);
+}
+
+// The same pass with its arguments read from a device descriptor when it
+// runs, so that one captured graph serves any batch written into it.
+template <int ROWS>
+__global__ void __launch_bounds__(kBlockThreads) batch_desc_kernel(const utf8_batch_desc* desc) {
+  const utf8_batch_desc d = *desc;
+  if (d.count <= 0) return;
+  batch_body<ROWS, false>(d.data, d.offsets, d.count, d.out_valid, nullptr);
+}
+
+// Sets the descriptor's count flags to 1 (the batch pass only clears them).
+__global__ void set_flags_desc_kernel(const utf8_batch_desc* desc) {
+  const int64_t count = desc->count;
+  uint8_t* out = desc->out_valid;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+    out[i] = 1;
+}
+
 template <int ROWS, bool LOCATE = false>
 static cudaError_t launch_batch_rows(const uint8_t* data, const int64_t* offsets, int64_t count,
                                      uint8_t* out_valid, int blocks_per_sm, int sm_count,
@@ -307,6 +333,20 @@ cudaError_t launch_batch(const uint8_t* data, const int64_t* offsets, int64_t co
     default: return launch_batch_rows<2>(data, offsets, count, out_valid, cfg.batch_blocks_per_sm,
                                          sm_count, st);
   }
+}
+
+cudaError_t launch_batch_desc(const utf8_batch_desc* desc, const LaunchCfg& cfg, int sm_count,
+                              cudaStream_t st) {
+  set_flags_desc_kernel<<<(unsigned)(sm_count * 4), 256, 0, st>>>(desc);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)(sm_count * cfg.batch_blocks_per_sm);
+  switch (cfg.batch_rows) {
+    case 8: batch_desc_kernel<8><<<grid, kBlockThreads, 0, st>>>(desc); break;
+    case 4: batch_desc_kernel<4><<<grid, kBlockThreads, 0, st>>>(desc); break;
+    default: batch_desc_kernel<2><<<grid, kBlockThreads, 0, st>>>(desc); break;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_batch_first_errors(const uint8_t* data, const int64_t* offsets, int64_t count,

@@ -66,6 +66,11 @@ int copy_blocks_per_sm(int rows, int wanted);
 cudaError_t launch_batch(const uint8_t* data, const int64_t* offsets, int64_t count,
                          uint8_t* out_valid, const LaunchCfg& cfg, int sm_count, cudaStream_t st);
 
+// utf8_validate_batch with its arguments read from the device descriptor
+// when the kernels run (batch.cu).
+cudaError_t launch_batch_desc(const utf8_batch_desc* desc, const LaunchCfg& cfg, int sm_count,
+                              cudaStream_t st);
+
 // Clears *out_ok unless offsets[0] >= 0 and offsets[0 .. count] is
 // non-decreasing (batch.cu).
 cudaError_t launch_check_offsets(const int64_t* offsets, int64_t count, uint8_t* out_ok,

@@ -430,3 +430,37 @@ def test_offsets_debug_mode_rejects_before_launch():
                        text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.split("\n")[:3] == ["[1, 1, 1]", "rejected 1", "rejected 1"], r.stdout
+
+
+def test_batch_descriptor_graph_replays_other_batches():
+    """One CUDA graph of utf8_validate_batch_desc, replayed after the device
+    descriptor is rewritten: other pointers and another count each time."""
+    rng = np.random.default_rng(61)
+    batches = []
+    for count in (1000, 37, 5000, 1):
+        lens = rng.integers(0, 300, count)
+        strings = []
+        for i, n in enumerate(lens):
+            s = synth.fill(int(n), synth.UNIFORM, seed=count + i)
+            if i % 4 == 1 and n:
+                synth.inject_any(s, synth.ERROR_CLASSES[i % 7], rng)
+            strings.append(s)
+        offsets = synth.offsets_of([s.size for s in strings])
+        data = np.concatenate(strings) if offsets[-1] else np.zeros(1, np.uint8)
+        d, o = dev(data), torch.from_numpy(offsets).cuda()
+        out = torch.full((count,), 7, dtype=torch.uint8, device="cuda")
+        batches.append((data, offsets, d, o, out))
+    desc = torch.tensor(u.batch_desc_values(*batches[0][2:]), dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    u.utf8_validate_batch_desc(desc, stream=s)  # first call outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        u.utf8_validate_batch_desc(desc, stream=s)
+    for data, offsets, d, o, out in batches:
+        desc.copy_(torch.tensor(u.batch_desc_values(d, o, out), dtype=torch.int64))
+        out.fill_(7)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), oracle.valid_batch(data[:offsets[-1]], offsets))
