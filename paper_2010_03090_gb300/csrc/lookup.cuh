@@ -3,7 +3,7 @@
 // The paper classifies every byte with three 16-entry tables, indexed by the
 // high nibble and the low nibble of the previous byte and the high nibble of
 // the current byte, AND-ed together (Section 6.1, Fig. 1, Table 7); it then
-// compares bit 7 ("two continuations in a row") with the positions where a
+// compares bit 7 (two continuations in a row) with the positions where a
 // 3- or 4-byte lead two or three bytes back requires one (Section 6.2), and
 // pads the end of the stream with ASCII zeros (Section 6.3).  Any non-zero
 // byte of  (byte_1_high & byte_1_low & byte_2_high) ^ must_be_2_3  is an error.
