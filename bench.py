@@ -415,6 +415,27 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     per_buf_ms = np.array([[a.elapsed_time(b) for a, b in row] for row in ev])
     value = whole_job_gbs(world, bytes_per_step, args.steps, elapsed_ms)
 
+    # end to end, on every rank at once: host buffers through the public
+    # host-memory entry point; all ranks' bytes over the slowest rank's time
+    e2e_steps = 1 if "e2e" in legs else 0
+    e2e_value, e2e_flags = None, flags
+    if e2e_steps:
+        pinned = []
+        for b in host:
+            p = torch.empty(b.size, dtype=torch.uint8, pin_memory=True)
+            p.numpy()[:] = b
+            pinned.append(p)
+        u.utf8_validate_host(pinned[0][: 1 << 20], stream=stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_flags = [u.utf8_validate_host(p, stream=stream) for p in pinned]
+        e2e_dt = max_over_ranks(time.perf_counter() - t, dist, "cuda")
+        e2e_value = world * bytes_per_step * e2e_steps / e2e_dt / 1e9
+        del pinned
+
     if rank != 0:
         if dist:
             dist.barrier()
@@ -441,24 +462,6 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     per_variant = {nm: round(host[i].size / (per_buf_ms[:, i].mean() / 1e3) / 1e9, 1)
                    for i, nm in enumerate(names)}
     cfg = json.loads(u.utf8_config_json())
-
-    # end to end: host buffers through the public host-memory entry point
-    e2e_steps = 1 if "e2e" in legs else 0
-    e2e_value, e2e_flags = None, flags
-    if e2e_steps:
-        pinned = []
-        for b in host:
-            p = torch.empty(b.size, dtype=torch.uint8, pin_memory=True)
-            p.numpy()[:] = b
-            pinned.append(p)
-        u.utf8_validate_host(pinned[0][: 1 << 20], stream=stream)
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        for _ in range(e2e_steps):
-            e2e_flags = [u.utf8_validate_host(p, stream=stream) for p in pinned]
-        e2e_dt = time.perf_counter() - t
-        e2e_value = bytes_per_step * e2e_steps / e2e_dt / 1e9
-        del pinned
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
