@@ -214,7 +214,7 @@ void worker_main(utf8_server* s) {
     if (progress) continue;
     if (busy_any) {  // batches on the GPU: poll again shortly
       lock.unlock();
-      std::this_thread::sleep_for(std::chrono::microseconds(5));
+      std::this_thread::sleep_for(std::chrono::microseconds(1));
     } else if (s->pending.empty()) {
       s->cv_work.wait_for(lock, std::chrono::milliseconds(5));
     } else {  // wait until the oldest request is old enough
