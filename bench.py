@@ -557,7 +557,59 @@ def bench_locate(u, torch, dev, names, stream, flags=None, steps: int = 30) -> d
         ok = ok and all((r == 0) == bool(f) for r, f in zip(rule, flags))
     return {"gbs": round(total / (ms / 1e3) / 1e9, 1), "steps": steps,
             "bytes_per_step": int(sum(sizes)), "kernels_per_buffer": 2,
-            "rules": dict(zip(names, rule)), "results_consistent": ok}
+            "rules": dict(zip(names, rule)), "results_consistent": ok,
+            "early_reject": bench_early_reject(u, torch, dev, names, stream)}
+
+
+def bench_early_reject(u, torch, dev, names, stream, reps: int = 7) -> dict:
+    """How fast invalid input is turned down: one clean buffer of the main
+    leg (CJK when present) as it is, with the byte 0xFF (never valid) at
+    offset 50, and the same size of uniformly random bytes; median of `reps`
+    calls (CUDA events) of validation with early exit off (the default) and
+    on, and of error location (which always stops early)."""
+    clean = dev[names.index("cjk")] if "cjk" in names else dev[0]
+    front = clean.clone()
+    front[50] = 0xFF
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    noise = torch.randint(0, 256, (clean.numel(),), dtype=torch.uint8, device="cuda",
+                          generator=g)
+    res = torch.empty(1, dtype=torch.uint8, device="cuda")
+    loc = torch.empty(2, dtype=torch.int64, device="cuda")
+
+    def median_ms(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                fn()
+            times = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                stream.synchronize()
+                times.append(a.elapsed_time(b))
+        return sorted(times)[reps // 2]
+
+    out = {"bytes": int(clean.numel()), "reps": reps}
+    answers = []
+    before = u.utf8_set_early_exit(False)
+    try:
+        for name, t in (("valid", clean), ("error_at_50", front), ("random_bytes", noise)):
+            u.utf8_set_early_exit(False)
+            v = median_ms(lambda: u.utf8_validate_async(t, res, stream=stream))
+            answers.append(int(res.item()))
+            u.utf8_set_early_exit(True)
+            v_early = median_ms(lambda: u.utf8_validate_async(t, res, stream=stream))
+            answers.append(int(res.item()))
+            loc_ms = median_ms(lambda: u.utf8_locate_error_async(t, loc, stream=stream))
+            out[name] = {"validate_ms": round(v, 4), "validate_early_exit_ms": round(v_early, 4),
+                         "locate_ms": round(loc_ms, 4),
+                         "position": int(u.error_info_fields(loc)[0][0].item())}
+    finally:
+        u.utf8_set_early_exit(before)
+    out["answers_ok"] = answers == [1, 1, 0, 0, 0, 0]
+    return out
 
 
 def bench_batch(u, torch, stream, peak: float, sample: int = 20000,

@@ -349,6 +349,22 @@ int utf8_tune_cache_save(const char* path);
  */
 int utf8_config_json(char* buf, size_t cap);
 
+/*
+ * Early exit of single-buffer validation (utf8_validate, utf8_validate_async,
+ * the host-memory calls), process-wide.  When on, the warps of the lookup
+ * pass look at the buffer's result byte every 16 KiB of their share and stop
+ * once another warp has found an error, so an invalid buffer whose first
+ * error lies early is rejected after reading a fraction of it.  The answer is
+ * the same either way; on valid text the polling loop runs about 2% slower,
+ * so the default is off.  The initial setting is the environment variable
+ * UTF8GPU_EARLY_EXIT (non-zero = on).  A launch takes the setting in force
+ * when it is issued; a captured CUDA graph keeps the one of its capture.
+ * Error location (utf8_locate_error*) always stops early: a warp whose
+ * remaining bytes all lie after an error already found stops.
+ * enable: 0 = off, anything else = on.  Returns the previous setting (0/1).
+ */
+int utf8_set_early_exit(int enable);
+
 #ifdef __cplusplus
 }
 #endif

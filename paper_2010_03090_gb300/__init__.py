@@ -15,6 +15,7 @@ from ._lib import (  # noqa: F401
     utf8_autotune,
     utf8_classify_debug,
     utf8_config_json,
+    utf8_set_early_exit,
     utf8_error_string,
     utf8_last_error,
     utf8_tune_cache_load,

@@ -19,7 +19,7 @@ EXPORTS = (
     "utf8_server_destroy", "utf8_validate_chunk", "utf8_stream_create", "utf8_stream_reset",
     "utf8_stream_update", "utf8_stream_finish", "utf8_stream_destroy", "utf8_copy_validate",
     "utf8_locate_error", "utf8_locate_error_async", "utf8_locate_errors_batch",
-    "utf8_check_offsets", "utf8_validate_batch_desc",
+    "utf8_check_offsets", "utf8_validate_batch_desc", "utf8_set_early_exit",
 )
 
 # Section 3's rules a-f as the library numbers them (enum utf8_rule).
@@ -74,6 +74,8 @@ def lib() -> ctypes.CDLL:
             L.utf8_tune_cache_save.restype = i32
             L.utf8_config_json.argtypes = [ctypes.c_char_p, sz]
             L.utf8_config_json.restype = i32
+            L.utf8_set_early_exit.argtypes = [i32]
+            L.utf8_set_early_exit.restype = i32
             L.utf8_validate_host_noalloc.argtypes = [vp, sz, vp]
             L.utf8_validate_host_noalloc.restype = ctypes.c_bool
             L.utf8_copy_validate.argtypes = [vp, vp, sz, vp, vp]
@@ -378,6 +380,12 @@ def utf8_tune_cache_load(path: str) -> None:
 
 def utf8_tune_cache_save(path: str) -> None:
     _check(lib().utf8_tune_cache_save(os.fsencode(path)), "utf8_tune_cache_save")
+
+
+def utf8_set_early_exit(enable: bool) -> bool:
+    """Switches early exit of single-buffer validation on or off (process-
+    wide); returns the previous setting."""
+    return bool(lib().utf8_set_early_exit(1 if enable else 0))
 
 
 def utf8_config_json() -> str:

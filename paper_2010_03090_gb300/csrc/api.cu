@@ -424,15 +424,20 @@ int utf8_config_json(char* buf, size_t cap) {
   const LaunchCfg cfg = config_of(*d);
   const int n = snprintf(tmp, sizeof tmp,
                          "{\"rows\": %d, \"blocks_per_sm\": %d, \"batch_rows\": %d, "
-                         "\"batch_blocks_per_sm\": %d, \"sm_count\": %d}",
+                         "\"batch_blocks_per_sm\": %d, \"sm_count\": %d, \"early_exit\": %d}",
                          cfg.rows, cfg.blocks_per_sm, cfg.batch_rows, cfg.batch_blocks_per_sm,
-                         d->sm_count);
+                         d->sm_count, early_exit_enabled() ? 1 : 0);
   if (buf != nullptr && cap > 0) {
     strncpy(buf, tmp, cap - 1);
     buf[cap - 1] = 0;
   }
   set_status(UTF8_OK);
   return n;
+}
+
+int utf8_set_early_exit(int enable) {
+  set_status(UTF8_OK);
+  return set_early_exit(enable);
 }
 
 }  // extern "C"

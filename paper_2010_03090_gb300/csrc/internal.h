@@ -32,6 +32,11 @@ cudaError_t launch_validate_tiles(const uint8_t* data, uint64_t n, uint64_t t_be
                                   int sm_count, cudaStream_t st);
 uint64_t tile_bytes(const LaunchCfg& cfg);
 
+// Early exit of the single-buffer validation kernel (utf8_set_early_exit):
+// process-wide, initially UTF8GPU_EARLY_EXIT (non-zero = on; off if unset).
+bool early_exit_enabled();
+int set_early_exit(int enable);  // returns the previous setting (0 or 1)
+
 cudaError_t launch_classify_debug(const uint8_t* data, uint64_t n, uint8_t* out_special,
                                   uint8_t* out_must23, cudaStream_t st);
 

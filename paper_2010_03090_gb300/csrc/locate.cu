@@ -30,16 +30,24 @@ __global__ void __launch_bounds__(kBlockThreads)
   const uint32_t merge_sel = carry_merge_selector(lane);
   Carry carry = ascii_carry();
   if (t0 > 0) carry = halo_carry(load_word(s, t0 * tb - 4));
-  uint64_t in0, in1;
-  interior_tiles<ROWS>(s, in0, in1);
+  const RunTiles run = run_tiles<ROWS>(s, t0, t1);
   const uint8_t* lane_ptr = s.abase + t0 * tb + lane * 16;
+  // Every kPollBytes the warp looks at the smallest position marked so far
+  // (loaded kPollBytes earlier, so the load's latency stays hidden): once it
+  // lies before the warp's next tile, no error the warp could still find is
+  // the first, and the warp stops.
+  constexpr uint32_t poll_tiles = kPollBytes / (uint32_t)tb;
+  static_assert(poll_tiles >= 1, "a poll falls after whole tiles");
+  const bool poll = poll_tiles < run.cnt;
+  uint64_t best = poll ? load_position(out) : ~uint64_t(0);
   uint4 next[ROWS];
-  load_tile<ROWS>(s, t0, in0, in1, lane, lane_ptr, next);
-  for (uint64_t t = t0; t < t1; ++t, lane_ptr += tb) {
+  load_run_tile<ROWS>(s, run, t0, 0, lane, lane_ptr, next);
+  uint32_t tiles_to_look = poll_tiles;
+  for (uint32_t k = 0; k < run.cnt; ++k, lane_ptr += tb) {
     uint4 d[ROWS];
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) d[r] = next[r];
-    if (t + 1 < t1) load_tile<ROWS>(s, t + 1, in0, in1, lane, lane_ptr + tb, next);
+    if (k + 1 < run.cnt) load_run_tile<ROWS>(s, run, t0, k + 1, lane, lane_ptr + tb, next);
     uint32_t e[ROWS / 2][8];
     check_tile<ROWS>(d, carry, lane, merge_sel, e);
     uint32_t any = 0;
@@ -50,8 +58,13 @@ __global__ void __launch_bounds__(kBlockThreads)
     if (__any_sync(kFull, any != 0)) {
       const uint32_t first = __reduce_min_sync(kFull, lane_first_error<ROWS>(e, lane));
       // virtual positions before s.off are zeros after zeros: never erroneous
-      if (lane == 0) mark_first_error(out, t * tb + first - s.off);
+      if (lane == 0) mark_first_error(out, (t0 + k) * tb + first - s.off);
       return;
+    }
+    if (poll && --tiles_to_look == 0) {  // (t0 + k + 1) * tb > s.off here
+      tiles_to_look = poll_tiles;
+      if (__any_sync(kFull, best < (t0 + k + 1) * tb - s.off)) return;
+      best = load_position(out);
     }
   }
 }

@@ -89,6 +89,14 @@ __device__ __forceinline__ void settle_location(const uint8_t* s, uint64_t n,
   out->reserved = 0;
 }
 
+// The position field as other warps of the grid leave it (GPU-scope relaxed
+// load, ordered with their atomic minima).
+__device__ __forceinline__ uint64_t load_position(const utf8_error_info* out) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(&out->position));
+  return v;
+}
+
 // Atomic minimum on a location's position field (set to all ones beforehand).
 __device__ __forceinline__ void mark_first_error(utf8_error_info* out, uint64_t position) {
   atomicMin(reinterpret_cast<unsigned long long*>(&out->position),

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     if (a >= b) continue;
     const Span s = make_span(segs[i].data, segs[i].len);
     const uint32_t err = warp_check_tiles<ROWS>(s, a, b);
-    if (__any_sync(kFull, err != 0) && lane == 0) out_valid[i] = 0;
+    if (__any_sync(kFull, err != 0) && lane == 0) clear_result(out_valid + i);
   }
 }
 

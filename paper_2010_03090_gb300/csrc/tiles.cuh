@@ -229,8 +229,64 @@ __device__ __forceinline__ uint32_t carry_merge_selector(int lane) {
   return lane == 0 ? 0x6341u : 0x7654u;
 }
 
-// Checks tiles [t_begin, t_end) of a stream with one warp; returns a non-zero
-// value in some lane iff an error lies in those tiles.
+// A result byte that several warps of one grid may clear while the others
+// still run: GPU-scope relaxed accesses, so that a store by one warp is seen by
+// the loads of the others (through L2, never a stale L1 line).  The byte is 1
+// before the launch and only ever cleared, so a warp that reads 0 knows the
+// answer is final.
+__device__ __forceinline__ uint32_t load_result(const uint8_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u8 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ void clear_result(uint8_t* p) {
+  asm volatile("st.relaxed.gpu.global.u8 [%0], %1;" ::"l"(p), "r"(0u));
+}
+
+// One warp's run of tiles [t_begin, t_begin + cnt) of a stream, counted from
+// t_begin in 32 bits (a run is far below 2^32 tiles): the run's interior
+// tiles are [i0, i0 + i_len).  With 32-bit counters the loop's own
+// bookkeeping takes fewer instructions from the ALU pipe that bounds the
+// classification.
+struct RunTiles {
+  uint32_t cnt;
+  uint32_t i0;
+  uint32_t i_len;
+};
+
+template <int ROWS>
+__device__ __forceinline__ RunTiles run_tiles(const Span& s, uint64_t t_begin, uint64_t t_end) {
+  uint64_t in0, in1;
+  interior_tiles<ROWS>(s, in0, in1);
+  RunTiles r;
+  r.cnt = t_end > t_begin ? (uint32_t)(t_end - t_begin) : 0u;
+  const uint64_t c0 = in0 > t_begin ? in0 - t_begin : 0;
+  const uint64_t c1 = in1 > t_begin ? in1 - t_begin : 0;
+  r.i0 = (uint32_t)(c0 < r.cnt ? c0 : r.cnt);
+  const uint32_t i1 = (uint32_t)(c1 < r.cnt ? c1 : r.cnt);
+  r.i_len = i1 > r.i0 ? i1 - r.i0 : 0u;
+  return r;
+}
+
+// Tile t_begin + k of a run; p = abase + (t_begin + k) * tile bytes + lane * 16.
+template <int ROWS>
+__device__ __forceinline__ void load_run_tile(const Span& s, const RunTiles& r, uint64_t t_begin,
+                                              uint32_t k, int lane, const uint8_t* p,
+                                              uint4 (&d)[ROWS]) {
+  if (k - r.i0 < r.i_len) load_tile_interior<ROWS>(p, d);
+  else load_tile_checked<ROWS>(s, t_begin + k, lane, d);
+}
+
+// Bytes a polling warp checks between two looks at a result.
+constexpr uint32_t kPollBytes = 16 << 10;
+
+// Checks tiles [t_begin, t_end) of a stream (t_begin <= t_end) with one warp;
+// returns a non-zero value in some lane iff an error lies in those tiles.
+// The next tile's loads are issued before the current tile is classified, so
+// their latency overlaps the ALU-bound classification.  Tile counts relative
+// to t_begin fit 32 bits (a run is far below 2^32 tiles); the interior tiles
+// of the run are [i0, i0 + i_len).
 template <int ROWS>
 __device__ __forceinline__ uint32_t warp_check_tiles(const Span& s, uint64_t t_begin,
                                                      uint64_t t_end) {
@@ -243,21 +299,78 @@ __device__ __forceinline__ uint32_t warp_check_tiles(const Span& s, uint64_t t_b
   uint64_t in0, in1;
   interior_tiles<ROWS>(s, in0, in1);
   const uint8_t* lane_ptr = s.abase + t_begin * tb + lane * 16;
-  // The next tile's loads are issued before the current tile is classified,
-  // so its memory latency overlaps the ALU-bound classification.
+  const uint32_t cnt = (uint32_t)(t_end - t_begin);
+  const uint64_t c0 = in0 > t_begin ? in0 - t_begin : 0;
+  const uint64_t c1 = in1 > t_begin ? in1 - t_begin : 0;
+  const uint32_t i0 = (uint32_t)(c0 < cnt ? c0 : cnt);
+  const uint32_t i1 = (uint32_t)(c1 < cnt ? c1 : cnt);
+  const uint32_t i_len = i1 > i0 ? i1 - i0 : 0;
+  const auto load_rel = [&](uint32_t k, const uint8_t* p, uint4 (&d)[ROWS]) {
+    if (k - i0 < i_len) load_tile_interior<ROWS>(p, d);
+    else load_tile_checked<ROWS>(s, t_begin + k, lane, d);
+  };
   uint4 next[ROWS];
-  if (t_begin < t_end) load_tile<ROWS>(s, t_begin, in0, in1, lane, lane_ptr, next);
-  for (uint64_t t = t_begin; t < t_end; ++t, lane_ptr += tb) {
+  if (cnt > 0) load_rel(0, lane_ptr, next);
+  for (uint32_t k = 0; k < cnt; ++k, lane_ptr += tb) {
     uint4 d[ROWS];
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) d[r] = next[r];
-    if (t + 1 < t_end) load_tile<ROWS>(s, t + 1, in0, in1, lane, lane_ptr + tb, next);
+    if (k + 1 < cnt) load_rel(k + 1, lane_ptr + tb, next);
     uint32_t e[ROWS / 2][8];
     check_tile<ROWS>(d, carry, lane, merge_sel, e);
 #pragma unroll
     for (int p = 0; p < ROWS / 2; ++p)
 #pragma unroll
       for (int m = 0; m < 8; ++m) err |= e[p][m];
+  }
+  return err;
+}
+
+// warp_check_tiles that stops early once the stream's answer is known to be
+// "invalid".  Every kPollBytes the warp votes on the errors it has found so
+// far and looks at the result byte it loaded kPollBytes earlier (so the
+// load's latency hides behind the classification), and leaves if either
+// shows an error; errors in the tiles it skips cannot change the answer.
+// The split loop costs about 2% of the classification rate on valid text
+// (the single loop above schedules better), so polling is the caller's choice.
+template <int ROWS>
+__device__ __forceinline__ uint32_t warp_check_tiles_polling(const Span& s, uint64_t t_begin,
+                                                             uint64_t t_end,
+                                                             const uint8_t* result) {
+  constexpr uint64_t tb = TileGeom<ROWS>::kBytes;
+  constexpr uint32_t poll_tiles = kPollBytes / (uint32_t)tb;
+  static_assert(poll_tiles >= 1, "a poll falls after whole tiles");
+  const int lane = threadIdx.x & (kLanes - 1);
+  uint32_t err = 0;
+  const uint32_t merge_sel = carry_merge_selector(lane);
+  Carry carry = ascii_carry();  // zeros before the stream
+  if (t_begin < t_end && t_begin > 0) carry = halo_carry(load_word(s, t_begin * tb - 4));
+  const RunTiles run = run_tiles<ROWS>(s, t_begin, t_end);
+  const uint8_t* lane_ptr = s.abase + t_begin * tb + lane * 16;
+  const bool poll = poll_tiles < run.cnt;
+  uint32_t seen = poll ? load_result(result) : 1u;
+  uint4 next[ROWS];
+  if (run.cnt > 0) load_run_tile<ROWS>(s, run, t_begin, 0, lane, lane_ptr, next);
+  uint32_t k = 0;
+  while (k < run.cnt) {
+    const uint32_t k_look = poll && run.cnt - k > poll_tiles ? k + poll_tiles : run.cnt;
+    for (; k < k_look; ++k, lane_ptr += tb) {
+      uint4 d[ROWS];
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) d[r] = next[r];
+      if (k + 1 < run.cnt)
+        load_run_tile<ROWS>(s, run, t_begin, k + 1, lane, lane_ptr + tb, next);
+      uint32_t e[ROWS / 2][8];
+      check_tile<ROWS>(d, carry, lane, merge_sel, e);
+#pragma unroll
+      for (int p = 0; p < ROWS / 2; ++p)
+#pragma unroll
+        for (int m = 0; m < 8; ++m) err |= e[p][m];
+    }
+    if (k < run.cnt) {  // only when polling
+      if (__any_sync(kFull, err != 0 || seen == 0)) break;
+      seen = load_result(result);
+    }
   }
   return err;
 }

@@ -4,9 +4,14 @@
 // each take one contiguous run of tiles of the buffer (Section 6's loop, one
 // loop per warp, the previous block carried in registers), OR their error
 // words and clear the result byte if any lane saw an error.  The result byte
-// is set to 1 beforehand on the same stream.
+// is set to 1 beforehand on the same stream.  With early exit switched on
+// (utf8_set_early_exit), warps also poll it and stop once another warp has
+// cleared it, so an invalid buffer is rejected without reading all of it.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
+
+#include <atomic>
 
 #include "internal.h"
 #include "tune.h"
@@ -16,7 +21,7 @@
 namespace utf8gpu {
 
 // Tiles [t_first, t_first + tiles) are split into one contiguous run per warp.
-template <int ROWS>
+template <int ROWS, bool POLL>
 __global__ void __launch_bounds__(kBlockThreads) validate_kernel(Span s, uint64_t t_first,
                                                                 uint64_t tiles,
                                                                 uint8_t* out_valid) {
@@ -24,8 +29,10 @@ __global__ void __launch_bounds__(kBlockThreads) validate_kernel(Span s, uint64_
   const uint64_t w = (uint64_t)blockIdx.x * (kBlockThreads / kLanes) + (threadIdx.x / kLanes);
   const uint64_t t0 = t_first + tiles * w / warps;
   const uint64_t t1 = t_first + tiles * (w + 1) / warps;
-  const uint32_t err = warp_check_tiles<ROWS>(s, t0, t1);
-  if (__any_sync(kFull, err != 0) && (threadIdx.x & (kLanes - 1)) == 0) *out_valid = 0;
+  uint32_t err;
+  if constexpr (POLL) err = warp_check_tiles_polling<ROWS>(s, t0, t1, out_valid);
+  else err = warp_check_tiles<ROWS>(s, t0, t1);
+  if (__any_sync(kFull, err != 0) && (threadIdx.x & (kLanes - 1)) == 0) clear_result(out_valid);
 }
 
 // One thread per 4-byte word of the virtual layout.
@@ -58,8 +65,32 @@ static cudaError_t launch_rows(const Span& s, uint64_t t_begin, uint64_t t_end,
   const uint64_t need = (tiles + warps_per_block - 1) / warps_per_block;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  validate_kernel<ROWS><<<(unsigned)grid, kBlockThreads, 0, st>>>(s, t_begin, tiles, out_valid);
+  if (early_exit_enabled())
+    validate_kernel<ROWS, true><<<(unsigned)grid, kBlockThreads, 0, st>>>(s, t_begin, tiles, out_valid);
+  else
+    validate_kernel<ROWS, false><<<(unsigned)grid, kBlockThreads, 0, st>>>(s, t_begin, tiles, out_valid);
   return cudaGetLastError();
+}
+
+namespace {
+std::atomic<int> g_early_exit{-1};  // -1: UTF8GPU_EARLY_EXIT not read yet
+}  // namespace
+
+bool early_exit_enabled() {
+  int v = g_early_exit.load(std::memory_order_relaxed);
+  if (v < 0) {
+    const char* e = getenv("UTF8GPU_EARLY_EXIT");
+    int unset = -1;
+    g_early_exit.compare_exchange_strong(unset, (e != nullptr && atoi(e) != 0) ? 1 : 0);
+    v = g_early_exit.load(std::memory_order_relaxed);
+  }
+  return v == 1;
+}
+
+int set_early_exit(int enable) {
+  const int before = early_exit_enabled() ? 1 : 0;
+  g_early_exit.store(enable ? 1 : 0);
+  return before;
 }
 
 uint64_t tile_bytes(const LaunchCfg& cfg) {
@@ -99,16 +130,28 @@ cudaError_t launch_classify_debug(const uint8_t* data, uint64_t n, uint8_t* out_
 
 namespace utf8gpu {
 
-int validate_blocks_per_sm(int rows) {
-  int n = 0;
-  cudaError_t e;
-  switch (rows) {
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, validate_kernel<2>, kBlockThreads, 0); break;
-    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, validate_kernel<8>, kBlockThreads, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, validate_kernel<4>, kBlockThreads, 0); break;
+// Resident CTAs per SM that both forms of the kernel (with and without
+// early exit) reach.
+template <int ROWS>
+static int validate_fit() {
+  int a = 0, b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, validate_kernel<ROWS, false>,
+                                                    kBlockThreads, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, validate_kernel<ROWS, true>,
+                                                    kBlockThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
   }
-  if (e != cudaSuccess) { cudaGetLastError(); return 1; }
+  const int n = a < b ? a : b;
   return n > 0 ? n : 1;
+}
+
+int validate_blocks_per_sm(int rows) {
+  switch (rows) {
+    case 2: return validate_fit<2>();
+    case 8: return validate_fit<8>();
+    default: return validate_fit<4>();
+  }
 }
 
 }  // namespace utf8gpu

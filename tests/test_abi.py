@@ -46,6 +46,23 @@ def test_error_strings():
     assert u.utf8_error_string(999) == "unknown status"
 
 
+def test_early_exit_setting_starts_from_the_environment():
+    """utf8_set_early_exit touches no device: its default comes from
+    UTF8GPU_EARLY_EXIT and it returns the previous setting."""
+    import sys
+    code = ("import paper_2010_03090_gb300 as u; "
+            "print(int(u.utf8_set_early_exit(True)), int(u.utf8_set_early_exit(False)), "
+            "int(u.utf8_set_early_exit(False)))")
+    for env, first in ((None, "0"), ("1", "1"), ("0", "0"), ("7", "1")):
+        e = dict(os.environ)
+        e.pop("UTF8GPU_EARLY_EXIT", None)
+        if env is not None:
+            e["UTF8GPU_EARLY_EXIT"] = env
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                             env=e, cwd=ROOT, check=True).stdout.split()
+        assert out == [first, "1", "0"], (env, out)
+
+
 def test_library_links_no_shared_runtime():
     out = subprocess.run(["readelf", "-d", u.lib_path()], capture_output=True, text=True).stdout
     assert "libcudart" not in out  # static CUDA runtime: only the driver is needed
