@@ -163,3 +163,55 @@ def front_error_timings():
     assert (int(pos[0]), int(rule[0])) == oracle.locate(buf)
     assert early < 0.5 * full, (early, full)
     assert early_loc < 0.5 * full_loc, (early_loc, full_loc)
+
+
+def test_graph_keeps_the_setting_of_its_capture(clean):
+    """A graph captured with early exit on replays the polling kernel after the
+    setting is switched off, and still gives the oracle's answers as the
+    buffer changes under it."""
+    buf, t = clean
+    out = torch.empty(1, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    before = u.utf8_set_early_exit(True)
+    try:
+        u.utf8_validate_async(t, out, stream=s)  # first call on this device outside capture
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            u.utf8_validate_async(t, out, stream=s)
+    finally:
+        u.utf8_set_early_exit(False)
+    try:
+        for positions in ([], [123], [N // 3], [N - 50]):
+            saved = with_errors(buf, t, positions, seed=3)
+            try:
+                out.fill_(7)
+                g.replay()
+                torch.cuda.synchronize()
+                assert int(out.item()) == int(oracle.valid(buf)), positions
+            finally:
+                undo(buf, t, saved)
+    finally:
+        u.utf8_set_early_exit(before)
+
+
+def test_every_length_and_alignment_with_early_exit_on():
+    """The polling kernel on short and medium buffers (no poll, or a few), at
+    every alignment, valid and with injected errors, against the oracle."""
+    rng = np.random.default_rng(71)
+    pool = torch.zeros(8 << 20, dtype=torch.uint8, device="cuda")
+    before = u.utf8_set_early_exit(True)
+    try:
+        sizes = list(range(0, 80)) + [int(x) for x in rng.integers(80, 6 << 20, 60)]
+        for n in sizes:
+            text = synth.fill(n, int(rng.integers(0, 7)), seed=n + 3)
+            if n and rng.random() < 0.6:
+                for _ in range(int(rng.integers(1, 4))):
+                    synth.inject_any(text, synth.ERROR_CLASSES[int(rng.integers(0, 7))], rng)
+            want = oracle.valid(text)
+            for shift in (0, 1, 7, 15):
+                if n:
+                    pool[shift:shift + n] = torch.from_numpy(text).cuda()
+                assert u.utf8_validate(pool[shift:shift + n]) == want, (n, shift)
+    finally:
+        u.utf8_set_early_exit(before)
