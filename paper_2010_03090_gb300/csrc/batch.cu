@@ -61,21 +61,40 @@ __device__ __forceinline__ void gather8(const uint8_t* data, int64_t x, int64_t 
   w_hi = __funnelshift_r(u[1], u[2], s8) & keep_bytes(ka - 4, kb - 4);
 }
 
-// First j in [lo, hi) with offsets[j] >= target (hi if none); whole warp.
-__device__ int64_t warp_lower_bound(const int64_t* offsets, int64_t lo, int64_t hi,
-                                    int64_t target) {
+// First j in [0, hi) with offsets[j] >= target (hi if none), for two targets
+// at once; whole warp (search.cuh gives the narrowing step).  Each round every
+// lane probes both ranges, so the two chains of dependent loads overlap: a
+// warp's start waits for the rounds of one search, not of two.
+__device__ void warp_lower_bound2(const int64_t* offsets, int64_t hi, int64_t target_a,
+                                  int64_t target_b, int64_t& res_a, int64_t& res_b) {
   const int lane = threadIdx.x & (kLanes - 1);
-  while (hi - lo > kLanes) {
-    const int64_t step = lb_step(lo, hi);
-    const int64_t j = lo + lane * step;
-    const bool ge = j < hi ? offsets[j] >= target : true;
-    const LbRange r = lb_narrow(lo, hi, step, __ballot_sync(kFull, ge));
-    lo = r.lo;
-    hi = r.hi;
+  int64_t lo_a = 0, hi_a = hi, lo_b = 0, hi_b = hi;
+  while (hi_a - lo_a > kLanes || hi_b - lo_b > kLanes) {
+    const bool open_a = hi_a - lo_a > kLanes, open_b = hi_b - lo_b > kLanes;
+    const int64_t step_a = lb_step(lo_a, hi_a), step_b = lb_step(lo_b, hi_b);
+    const int64_t ja = lo_a + lane * step_a, jb = lo_b + lane * step_b;
+    const bool ge_a = open_a && ja < hi_a ? offsets[ja] >= target_a : true;
+    const bool ge_b = open_b && jb < hi_b ? offsets[jb] >= target_b : true;
+    const uint32_t mask_a = __ballot_sync(kFull, ge_a);
+    const uint32_t mask_b = __ballot_sync(kFull, ge_b);
+    if (open_a) {
+      const LbRange r = lb_narrow(lo_a, hi_a, step_a, mask_a);
+      lo_a = r.lo;
+      hi_a = r.hi;
+    }
+    if (open_b) {
+      const LbRange r = lb_narrow(lo_b, hi_b, step_b, mask_b);
+      lo_b = r.lo;
+      hi_b = r.hi;
+    }
   }
-  const int64_t j = lo + lane;
-  const bool ge = j < hi ? offsets[j] >= target : true;
-  return lb_final(lo, hi, __ballot_sync(kFull, ge));
+  const int64_t ja = lo_a + lane, jb = lo_b + lane;
+  const bool ge_a = ja < hi_a ? offsets[ja] >= target_a : true;
+  const bool ge_b = jb < hi_b ? offsets[jb] >= target_b : true;
+  const uint32_t mask_a = __ballot_sync(kFull, ge_a);
+  const uint32_t mask_b = __ballot_sync(kFull, ge_b);
+  res_a = lb_final(lo_a, hi_a, mask_a);
+  res_b = lb_final(lo_b, hi_b, mask_b);
 }
 
 // An error at `rel` bytes into string j: its flag is cleared, or (LOCATE) its
@@ -114,8 +133,8 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
   const int64_t range_lo = vbase + (int64_t)(t0 * kTileBytes);
   const int64_t range_hi = vbase + (int64_t)(t1 * kTileBytes);
   // boundaries of this warp: offsets[j] in [range_lo, range_hi), j in [b0, b1)
-  const int64_t b0 = warp_lower_bound(offsets, 0, count + 1, range_lo);
-  const int64_t b1 = warp_lower_bound(offsets, b0, count + 1, range_hi);
+  int64_t b0, b1;
+  warp_lower_bound2(offsets, count + 1, range_lo, range_hi, b0, b1);
   // strings that can hold a position of this warp: b0 - 1 .. b1 - 1
   const int64_t own_hi = b1 < count ? b1 : count;
 

@@ -35,6 +35,40 @@ static int64_t warp_lower_bound_host(const std::vector<int64_t>& a, int64_t lo, 
   return lb_final(lo, hi, mask);
 }
 
+// The batch kernel's two searches in one loop (warp_lower_bound2): both
+// ranges are probed each round, a range stops narrowing once it is at most
+// 32 wide, and both finish with one more probe round.
+static void warp_lower_bound2_host(const std::vector<int64_t>& a, int64_t hi, int64_t ta,
+                                   int64_t tb, int64_t* ra, int64_t* rb, int* rounds) {
+  int64_t lo_a = 0, hi_a = hi, lo_b = 0, hi_b = hi;
+  *rounds = 0;
+  auto probe = [&](int64_t lo, int64_t h, int64_t step, int64_t t) {
+    uint32_t mask = 0;
+    for (int k = 0; k < 32; ++k) {
+      const int64_t j = lo + k * step;
+      if (j >= h || a[j] >= t) mask |= 1u << k;
+    }
+    return mask;
+  };
+  while (hi_a - lo_a > 32 || hi_b - lo_b > 32) {
+    if (hi_a - lo_a > 32) {
+      const int64_t s = lb_step(lo_a, hi_a);
+      const LbRange r = lb_narrow(lo_a, hi_a, s, probe(lo_a, hi_a, s, ta));
+      lo_a = r.lo;
+      hi_a = r.hi;
+    }
+    if (hi_b - lo_b > 32) {
+      const int64_t s = lb_step(lo_b, hi_b);
+      const LbRange r = lb_narrow(lo_b, hi_b, s, probe(lo_b, hi_b, s, tb));
+      lo_b = r.lo;
+      hi_b = r.hi;
+    }
+    if (++*rounds > 64) break;
+  }
+  *ra = lb_final(lo_a, hi_a, probe(lo_a, hi_a, 1, ta));
+  *rb = lb_final(lo_b, hi_b, probe(lo_b, hi_b, 1, tb));
+}
+
 int main() {
   std::mt19937_64 rng(20100309);
   int64_t checks = 0, bad = 0;
@@ -56,6 +90,18 @@ int main() {
       if (got != want) {
         if (bad < 10) printf("lower_bound n=%lld target=%lld got=%lld want=%lld\n",
                              (long long)n, (long long)target, (long long)got, (long long)want);
+        ++bad;
+      }
+      // both searches of a warp at once: this target and a second one
+      const int64_t target_b = target + (int64_t)(rng() % 5000);
+      int64_t ra = 0, rb = 0;
+      warp_lower_bound2_host(a, n, target, target_b, &ra, &rb, &rounds);
+      const int64_t want_b = std::lower_bound(a.begin(), a.end(), target_b) - a.begin();
+      ++checks;
+      if (ra != want || rb != want_b || rounds > 8) {
+        if (bad < 10) printf("lower_bound2 n=%lld targets=%lld,%lld got=%lld,%lld want=%lld,%lld\n",
+                             (long long)n, (long long)target, (long long)target_b, (long long)ra,
+                             (long long)rb, (long long)want, (long long)want_b);
         ++bad;
       }
       // last_at_most over a sub-range
