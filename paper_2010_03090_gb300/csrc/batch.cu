@@ -198,7 +198,7 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
       else load_tile_checked<ROWS>(region, t0 + i + 1, lane, next);
     }
     uint32_t e[ROWS / 2][8];
-    check_tile<ROWS, true>(d, carry, lane, merge_sel, e);
+    check_tile<ROWS>(d, carry, lane, merge_sel, e);
     uint32_t any_err = 0;
 #pragma unroll
     for (int p = 0; p < ROWS / 2; ++p)

@@ -167,31 +167,21 @@ __device__ __forceinline__ void interior_tiles(const Span& s, uint64_t& first, u
 // 2m+1, row 2p+1 byte 2m+1) of this lane's granules.  `carry` describes the
 // bytes before the tile (lane 0) and is updated.
 //
-// SAMPLED: the all-ASCII test first votes on the tile's first row (512
-// bytes) alone; on text with non-ASCII characters that row almost always
-// holds one, and the tile goes straight to the classification without OR-ing
-// its other rows.  It pays in the batch kernel (+0.5% on 1M short strings,
-// +1.3% on long ones); in the single-buffer loops the extra branch schedules
-// worse than the OR costs (-0.7%), so they test the whole tile.
-template <int ROWS, bool SAMPLED = false>
+// The all-ASCII test first votes on the tile's first row (512 bytes) alone:
+// on text with non-ASCII characters that row almost always holds one, and the
+// tile goes straight to the classification without OR-ing its other rows;
+// only a tile whose first row is ASCII pays for the full test.
+template <int ROWS>
 __device__ __forceinline__ void check_tile(const uint4 (&d)[ROWS], Carry& carry, int lane,
                                            uint32_t merge_sel, uint32_t (&e)[ROWS / 2][8]) {
   static_assert(ROWS % 2 == 0, "rows are processed in pairs");
   const int left = (lane + kLanes - 1) & (kLanes - 1);
-  bool ascii;
-  if constexpr (SAMPLED) {
-    const uint32_t sample = d[0].x | d[0].y | d[0].z | d[0].w;
-    ascii = false;
-    if (!__any_sync(kFull, sample & 0x80808080u)) {
-      uint32_t high = sample;
+  const uint32_t sample = d[0].x | d[0].y | d[0].z | d[0].w;
+  bool ascii = false;
+  if (!__any_sync(kFull, sample & 0x80808080u)) {
+    uint32_t high = sample;
 #pragma unroll
-      for (int r = 1; r < ROWS; ++r) high |= d[r].x | d[r].y | d[r].z | d[r].w;
-      ascii = !__any_sync(kFull, high & 0x80808080u);
-    }
-  } else {
-    uint32_t high = 0;
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r) high |= d[r].x | d[r].y | d[r].z | d[r].w;
+    for (int r = 1; r < ROWS; ++r) high |= d[r].x | d[r].y | d[r].z | d[r].w;
     ascii = !__any_sync(kFull, high & 0x80808080u);
   }
   if (ascii) {
