@@ -42,14 +42,15 @@ NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6800.0
 METRIC = "validated GB/s"
 # Integer ALU-pipe operations (LOP3, PRMT, SHF) the method needs per input
-# byte, as designed, for one 8-byte interleaved pair: selectors 7 (one right
-# shift, 3 bit selects, 3 half-word shifts), ASCII masks 2, table lookups 10,
-# merges 6, the prev1/prev2/prev3 checks 8, the error fold 1 and the
-# all-ASCII test 1: 35 operations (8 SHF, 12 PRMT, 15 LOP3).  The three left
-# shifts of a pair run on the FMA pipe (IMAD) and are not counted; the carry
-# between row pairs, loop and load overhead are excluded.  The ALU pipe issues
-# 64 such operations per clock per SM.
-ALU_OPS_PER_BYTE = 35 / 8
+# byte of non-ASCII text, as designed, for one 8-byte interleaved pair:
+# selectors 7 (one right shift, 3 bit selects, 3 half-word shifts), ASCII
+# masks 2, table lookups 10, merges 6, the prev1/prev2/prev3 checks 8 and the
+# error fold 1: 34 operations (8 SHF, 12 PRMT, 14 LOP3); plus the tile's
+# all-ASCII test on its first row, 2 LOP3 per 16 pairs.  The three left shifts
+# of a pair run on the FMA pipe (IMAD) and are not counted; the carry between
+# row pairs, loop and load overhead are excluded.  The ALU pipe issues 64 such
+# operations per clock per SM.
+ALU_OPS_PER_BYTE = (34 + 2 / 16) / 8
 ALU_LANES_PER_SM = 64
 WORKLOAD = ("single 1 GiB buffers: 5 seeded content variants (ascii, latin, cjk, emoji, "
             "uniform 1-4 byte) + a truncated-tail copy of each = 10 GiB per step")
