@@ -226,3 +226,31 @@ def test_buffer_beyond_4gib():
     assert want[0] > (1 << 32) and want[1] == 4
     assert u.utf8_validate(t) == oracle.valid(buf) == False  # noqa: E712
     assert u.utf8_locate_error(t) == want
+
+
+def test_batch_beyond_4gib():
+    """A batch of about 4.5 GiB (Pareto lengths, CJK and emoji content) whose
+    string offsets pass 2^32, with 2% of the strings corrupted, errors placed
+    near 2 KiB and 64 KiB multiples: flags and error locations against the
+    oracle, in the launch configuration the benchmark uses."""
+    data, offsets, _ = synth.workload_heavy_skew(seed=synth.SEED_BASE + 3100, count=4000,
+                                                   total=(9 << 29) + 777)
+    assert offsets[-1] > (1 << 32)
+    rng = np.random.default_rng(5)
+    more = synth.corrupt_strings(data, offsets, 0.02, seed=91, at_boundaries=[2048, 65536])
+    # strings that straddle or follow the 2^32 offset hold errors too
+    late = np.nonzero(offsets[:-1] >= (1 << 32) - (64 << 20))[0]
+    for i in late[::7]:
+        lo, hi = int(offsets[i]), int(offsets[i + 1])
+        if hi > lo:
+            synth.inject_any(data, synth.ERROR_CLASSES[int(rng.integers(0, 7))], rng, lo, hi)
+    d = torch.from_numpy(data).cuda()
+    o = torch.from_numpy(offsets).cuda()
+    flags = u.utf8_validate_batch(d, o).cpu().numpy()
+    want = oracle.valid_batch(data, offsets, threads=THREADS)
+    assert np.array_equal(flags.astype(bool), want.astype(bool))
+    assert (~want.astype(bool)).sum() >= len(more) // 2
+    pos, rule = u.error_info_fields(u.utf8_locate_errors_batch(d, o))
+    want_pos, want_rule = oracle.locate_batch(data, offsets, threads=THREADS)
+    assert np.array_equal(pos.cpu().numpy(), want_pos)
+    assert np.array_equal(rule.cpu().numpy(), want_rule)
