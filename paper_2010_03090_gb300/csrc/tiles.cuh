@@ -296,7 +296,9 @@ constexpr uint32_t kPollBytes = 16 << 10;
 // The next tile's loads are issued before the current tile is classified, so
 // their latency overlaps the ALU-bound classification.  Tile counts relative
 // to t_begin fit 32 bits (a run is far below 2^32 tiles); the interior tiles
-// of the run are [i0, i0 + i_len).
+// of the run are [i0, i0 + i_len).  The run is set up here as in run_tiles,
+// written out: through run_tiles and load_run_tile this loop compiled 0.8%
+// slower.
 template <int ROWS>
 __device__ __forceinline__ uint32_t warp_check_tiles(const Span& s, uint64_t t_begin,
                                                      uint64_t t_end) {
