@@ -54,7 +54,8 @@ __device__ __forceinline__ void mask_positions(uint32_t (&e)[ROWS / 2][8], uint6
       }
 }
 
-constexpr int kChunkRows = 8;  // tile rows per warp (4 KiB tiles), as the single-buffer default
+constexpr int kChunkRows = 8;       // tile rows per warp (4 KiB tiles), as the single-buffer default
+constexpr int kSmallChunkRows = 2;  // 1 KiB tiles for chunks too small to fill the grid
 
 template <int ROWS>
 __global__ void __launch_bounds__(kBlockThreads) chunk_kernel(Span s, uint64_t tiles, ChunkArgs a) {
@@ -121,11 +122,13 @@ __global__ void __launch_bounds__(kBlockThreads) chunk_kernel(Span s, uint64_t t
 
 // Resident CTAs per SM of chunk_kernel (the same on every GPU of this
 // architecture; computed once, thread-safely).
+// Resident CTAs per SM of chunk_kernel<ROWS>.
+template <int ROWS>
 static int chunk_blocks_per_sm() {
   static const int n = [] {
     int k = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, chunk_kernel<kChunkRows>, kBlockThreads,
-                                                      0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, chunk_kernel<ROWS>, kBlockThreads, 0) !=
+        cudaSuccess) {
       cudaGetLastError();
       k = 1;
     }
@@ -134,20 +137,32 @@ static int chunk_blocks_per_sm() {
   return n;
 }
 
-cudaError_t launch_chunk(const uint8_t* data, uint64_t n, uint32_t prefix,
-                         const uint8_t* prefix_dev, int final_chunk, uint8_t* out_valid,
-                         uint8_t* tail_out, int sm_count, cudaStream_t st) {
-  constexpr int ROWS = kChunkRows;
-  const Span s = make_span(data, n);
+template <int ROWS>
+static cudaError_t launch_chunk_rows(const Span& s, const ChunkArgs& a, int sm_count,
+                                     cudaStream_t st) {
   const uint64_t tiles = span_tiles<ROWS>(s);
   const uint64_t warps_per_block = kBlockThreads / kLanes;
-  uint64_t grid = (uint64_t)sm_count * (uint64_t)chunk_blocks_per_sm();
+  uint64_t grid = (uint64_t)sm_count * (uint64_t)chunk_blocks_per_sm<ROWS>();
   const uint64_t need = (tiles + warps_per_block - 1) / warps_per_block;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  ChunkArgs a{prefix, prefix_dev, final_chunk, out_valid, tail_out};
   chunk_kernel<ROWS><<<(unsigned)grid, kBlockThreads, 0, st>>>(s, tiles, a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_chunk(const uint8_t* data, uint64_t n, uint32_t prefix,
+                         const uint8_t* prefix_dev, int final_chunk, uint8_t* out_valid,
+                         uint8_t* tail_out, int sm_count, cudaStream_t st) {
+  const Span s = make_span(data, n);
+  const ChunkArgs a{prefix, prefix_dev, final_chunk, out_valid, tail_out};
+  // A chunk with fewer 4 KiB tiles than the persistent grid has warps leaves
+  // SMs idle: it is checked in 1 KiB tiles instead, spread over four times
+  // as many warps.
+  const uint64_t grid_warps = (uint64_t)sm_count * (uint64_t)chunk_blocks_per_sm<kChunkRows>() *
+                              (kBlockThreads / kLanes);
+  if (span_tiles<kChunkRows>(s) < grid_warps)
+    return launch_chunk_rows<kSmallChunkRows>(s, a, sm_count, st);
+  return launch_chunk_rows<kChunkRows>(s, a, sm_count, st);
 }
 
 }  // namespace utf8gpu

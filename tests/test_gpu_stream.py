@@ -141,3 +141,37 @@ def test_stream_sequence_in_cuda_graph():
         assert int(out.item()) == int(oracle.valid(bad)) == 0
     finally:
         u.utf8_stream_destroy(h)
+
+
+def test_chunks_on_both_sides_of_the_tile_switch():
+    """Chunks that fill the grid with 4 KiB tiles (about 10 MB and up) and
+    smaller ones, which use 1 KiB tiles, cut inside characters, with errors
+    in either kind of chunk, at the cut and at the end; stateless chunks and
+    the stream state both equal the whole buffer."""
+    rng = np.random.default_rng(17)
+    base = synth.fill(40 << 20, synth.UNIFORM, seed=17)
+    cuts = [0, 3, (12 << 20) + 1, (12 << 20) + 5001, (30 << 20) + 7, (31 << 20) + 2, base.size]
+    h = u.utf8_stream_create()
+    try:
+        for bad_at in (None, 5 << 20, (12 << 20) + 2, (20 << 20) + 11, (30 << 20) + 5,
+                       base.size - 2):
+            b = base.copy()
+            if bad_at is not None:
+                synth.inject_any(b, synth.ERROR_CLASSES[int(rng.integers(0, 7))], rng, at=bad_at)
+            want = oracle.valid(b)
+            d = torch.from_numpy(b).cuda()
+            flag = torch.ones(1, dtype=torch.uint8, device="cuda")
+            for k in range(len(cuts) - 1):
+                lo, hi = cuts[k], cuts[k + 1]
+                u.utf8_validate_chunk(d[lo:hi], bytes(b[max(0, lo - 3):lo]), k == len(cuts) - 2,
+                                      flag)
+            u.utf8_stream_reset(h)
+            for k in range(len(cuts) - 1):
+                u.utf8_stream_update(h, d[cuts[k]:cuts[k + 1]])
+            out = torch.zeros(1, dtype=torch.uint8, device="cuda")
+            u.utf8_stream_finish(h, out)
+            torch.cuda.synchronize()
+            assert flag.item() == want, bad_at
+            assert out.item() == want, bad_at
+    finally:
+        u.utf8_stream_destroy(h)
