@@ -64,7 +64,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--buffer-bytes", type=int, default=GIB)
     ap.add_argument("--no-extras", action="store_true", help="skip batch/serving extras")
-    ap.add_argument("--legs", default="main,e2e,cpu,locate,batch,serve,stream,copy",
+    ap.add_argument("--legs", default="main,e2e,cpu,locate,batch,serve,stream,copy,small",
                     help="comma-separated legs to run (profiling runs pick one)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-memory leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
@@ -348,7 +348,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if args.no_cpu:
         legs.discard("cpu")
     if args.no_extras:
-        legs -= {"locate", "batch", "serve", "stream", "copy"}
+        legs -= {"locate", "batch", "serve", "stream", "copy", "small"}
     if "main" not in legs:  # a single secondary leg (profiling runs)
         torch.cuda.set_device(local_rank)
         u.lib()
@@ -366,6 +366,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             out["serving"] = bench_serving(torch, args.serve_seconds)
         if "stream" in legs:
             out["streaming"] = bench_stream(u, torch)
+        if "small" in legs:
+            out["small_buffers"] = bench_small(u, torch)
         if "copy" in legs:
             out["copy_validate"] = bench_copy(u, torch)
         print(json.dumps(out), flush=True)
@@ -513,7 +515,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         line["cpu_baseline"] = oracle_baseline(host, names, args.cpu_seconds)
     if world == 1 and "locate" in legs:
         line["locate"] = bench_locate(u, torch, dev, names, stream, flags)
-    if world == 1 and legs & {"batch", "serve", "stream", "copy"}:
+    if world == 1 and legs & {"batch", "serve", "stream", "copy", "small"}:
         del dev
         torch.cuda.empty_cache()
         if "batch" in legs:
@@ -523,6 +525,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             line["serving"] = bench_serving(torch, args.serve_seconds)
         if "stream" in legs:
             line["streaming"] = bench_stream(u, torch)
+        if "small" in legs:
+            line["small_buffers"] = bench_small(u, torch)
         if "copy" in legs:
             line["copy_validate"] = bench_copy(u, torch)
     print(json.dumps(line), flush=True)
@@ -768,6 +772,32 @@ def bench_stream(u, torch) -> dict:
     torch.cuda.synchronize()
     res["whole_buffer_gbs"] = round(d.numel() * 5 / (a.elapsed_time(b) / 1e3) / 1e9, 1)
     return res
+
+
+def bench_small(u, torch, reps: int = 50) -> dict:
+    """Latency of one utf8_validate_async on a small CJK-like buffer (64 KiB,
+    1 MiB, 8 MiB): the median over `reps` calls of the device time between
+    CUDA events around the call (the 1-byte memset and the kernel)."""
+    import synth
+    out = {"reps": reps}
+    s = torch.cuda.Stream()
+    res = torch.empty(1, dtype=torch.uint8, device="cuda")
+    for n in (64 << 10, 1 << 20, 8 << 20):
+        d = torch.from_numpy(synth.fill_variant(n, "cjk", synth.SEED_BASE + 6000)).cuda()
+        times = []
+        with torch.cuda.stream(s):
+            for i in range(reps + 5):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                u.utf8_validate_async(d, res, stream=s)
+                b.record(s)
+                s.synchronize()
+                if i >= 5:
+                    times.append(a.elapsed_time(b) * 1e3)
+        key = f"{n >> 10}KiB" if n < (1 << 20) else f"{n >> 20}MiB"
+        out[key + "_us"] = round(sorted(times)[reps // 2], 2)
+        out[key + "_valid"] = int(res.item())
+    return out
 
 
 def bench_copy(u, torch) -> dict:

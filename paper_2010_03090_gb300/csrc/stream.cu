@@ -155,12 +155,12 @@ cudaError_t launch_chunk(const uint8_t* data, uint64_t n, uint32_t prefix,
                          uint8_t* tail_out, int sm_count, cudaStream_t st) {
   const Span s = make_span(data, n);
   const ChunkArgs a{prefix, prefix_dev, final_chunk, out_valid, tail_out};
-  // A chunk with fewer 4 KiB tiles than the persistent grid has warps leaves
-  // SMs idle: it is checked in 1 KiB tiles instead, spread over four times
-  // as many warps.
+  // A chunk so small that its 1 KiB tiles number at most the warps of the
+  // persistent grid is checked in 1 KiB tiles: 4 KiB tiles would leave SMs
+  // idle.
   const uint64_t grid_warps = (uint64_t)sm_count * (uint64_t)chunk_blocks_per_sm<kChunkRows>() *
                               (kBlockThreads / kLanes);
-  if (span_tiles<kChunkRows>(s) < grid_warps)
+  if (span_tiles<kSmallChunkRows>(s) <= grid_warps)
     return launch_chunk_rows<kSmallChunkRows>(s, a, sm_count, st);
   return launch_chunk_rows<kChunkRows>(s, a, sm_count, st);
 }

@@ -102,7 +102,17 @@ cudaError_t launch_validate_tiles(const uint8_t* data, uint64_t n, uint64_t t_be
                                   uint64_t t_end, uint8_t* out_valid, const LaunchCfg& cfg,
                                   int sm_count, cudaStream_t st) {
   const Span s = make_span(data, n);
-  switch (cfg.rows) {
+  int rows = cfg.rows;
+  // A whole buffer so small that its 1 KiB tiles number at most the warps of
+  // the persistent grid is checked in 1 KiB tiles: larger tiles would leave
+  // SMs idle.  (A range of tiles keeps the configured height, in which the
+  // caller counts its tiles.)
+  if (t_begin == 0 && t_end == ~uint64_t(0) && rows != 2) {
+    const uint64_t grid_warps =
+        (uint64_t)sm_count * (uint64_t)cfg.blocks_per_sm * (kBlockThreads / kLanes);
+    if (span_tiles<2>(s) <= grid_warps) rows = 2;
+  }
+  switch (rows) {
     case 2: return launch_rows<2>(s, t_begin, t_end, out_valid, cfg, sm_count, st);
     case 8: return launch_rows<8>(s, t_begin, t_end, out_valid, cfg, sm_count, st);
     default: return launch_rows<4>(s, t_begin, t_end, out_valid, cfg, sm_count, st);

@@ -144,17 +144,17 @@ def test_stream_sequence_in_cuda_graph():
 
 
 def test_chunks_on_both_sides_of_the_tile_switch():
-    """Chunks that fill the grid with 4 KiB tiles (about 10 MB and up) and
-    smaller ones, which use 1 KiB tiles, cut inside characters, with errors
-    in either kind of chunk, at the cut and at the end; stateless chunks and
-    the stream state both equal the whole buffer."""
+    """Chunks checked in 4 KiB tiles and chunks small enough (about 2.4 MB
+    and less on 152 SMs) to be checked in 1 KiB tiles, cut inside
+    characters, with errors in either kind of chunk, at the cut and at the
+    end; stateless chunks and the stream state both equal the whole buffer."""
     rng = np.random.default_rng(17)
     base = synth.fill(40 << 20, synth.UNIFORM, seed=17)
     cuts = [0, 3, (12 << 20) + 1, (12 << 20) + 5001, (30 << 20) + 7, (31 << 20) + 2, base.size]
     h = u.utf8_stream_create()
     try:
         for bad_at in (None, 5 << 20, (12 << 20) + 2, (20 << 20) + 11, (30 << 20) + 5,
-                       base.size - 2):
+                       (30 << 20) + 100, base.size - 2):
             b = base.copy()
             if bad_at is not None:
                 synth.inject_any(b, synth.ERROR_CLASSES[int(rng.integers(0, 7))], rng, at=bad_at)
