@@ -41,17 +41,10 @@ GIB = 1 << 30
 NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6800.0
 METRIC = "validated GB/s"
-# Integer ALU-pipe operations (LOP3, PRMT, SHF) the method needs per input
-# byte of non-ASCII text, as designed, for one 8-byte interleaved pair:
-# selectors 7 (one right shift, 3 bit selects, 3 half-word shifts), ASCII
-# masks 2, table lookups 10, merges 6, the prev1/prev2/prev3 checks 8 and the
-# error fold 1: 34 operations (8 SHF, 12 PRMT, 14 LOP3); plus the tile's
-# all-ASCII test on its first row, 2 LOP3 per 16 pairs.  The three left shifts
-# of a pair run on the FMA pipe (IMAD) and are not counted; the carry between
-# row pairs, loop and load overhead are excluded.  The ALU pipe issues 64 such
-# operations per clock per SM.
-ALU_OPS_PER_BYTE = (34 + 2 / 16) / 8
-ALU_LANES_PER_SM = 64
+# Integer ALU-pipe operations (LOP3, PRMT, SHF) per byte of non-ASCII text,
+# as the kernel's design counts them (used only when no ncu count taken on
+# the current kernel sources is on record in profiles/traffic.json).
+ALU_OPS_PER_BYTE_DESIGN = (34 + 2 / 16) / 8
 WORKLOAD = ("single 1 GiB buffers: 5 seeded content variants (ascii, latin, cjk, emoji, "
             "uniform 1-4 byte) + a truncated-tail copy of each = 10 GiB per step")
 
@@ -64,7 +57,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--buffer-bytes", type=int, default=GIB)
     ap.add_argument("--no-extras", action="store_true", help="skip batch/serving extras")
-    ap.add_argument("--legs", default="main,e2e,cpu,locate,batch,serve,stream,copy,small",
+    ap.add_argument("--legs", default="main,e2e,cpu,alu,cfg1mib,locate,batch,serve,stream,copy,small",
                     help="comma-separated legs to run (profiling runs pick one)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-memory leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
@@ -217,6 +210,32 @@ def source_hash(files=("lookup.cuh", "tiles.cuh", "validate.cu")) -> str:
     return h.hexdigest()[:16]
 
 
+def alu_probe(blocks_per_sm: int = 8, iters: int = 20000) -> dict:
+    """Operations per clock per SM of the integer pipes (LOP3, PRMT, SHF on
+    the ALU pipe; IMAD on the FMA pipe; PRMT and IMAD mixed), measured now by
+    the probe kernel: the denominator of the integer-ALU roofline."""
+    import ctypes
+    from paper_2010_03090_gb300 import build as cuda_build
+    L = ctypes.CDLL(cuda_build.build_probe())
+    L.alu_probe_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint,
+                                ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_int)]
+    L.alu_probe_run.restype = ctypes.c_int
+    out = {}
+    for op, name in enumerate(("lop3", "prmt", "shf", "imad", "prmt+imad")):
+        ops, sms = ctypes.c_double(), ctypes.c_int()
+        cyc = np.zeros(4096, np.int64)
+        for _ in range(2):  # the first run warms up
+            rc = L.alu_probe_run(op, blocks_per_sm, iters, cyc.ctypes.data, ctypes.byref(ops),
+                                 ctypes.byref(sms))
+            if rc != 0:
+                return {"error": f"probe failed: CUDA error {rc}"}
+        spans = cyc[: blocks_per_sm * sms.value]
+        out[name] = round(ops.value * blocks_per_sm / float(np.median(spans)), 2)
+    out["unit"] = "thread operations per clock per SM (median block cycle span)"
+    return out
+
+
 def oracle_baseline(bufs, names, seconds: float) -> dict:
     """The oracle, single-threaded, on the tail of every buffer (from a
     character start, so each sample's validity equals its buffer's)."""
@@ -348,7 +367,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if args.no_cpu:
         legs.discard("cpu")
     if args.no_extras:
-        legs -= {"locate", "batch", "serve", "stream", "copy", "small"}
+        legs -= {"locate", "batch", "serve", "stream", "copy", "small", "cfg1mib"}
     if "main" not in legs:  # a single secondary leg (profiling runs)
         torch.cuda.set_device(local_rank)
         u.lib()
@@ -368,6 +387,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             out["streaming"] = bench_stream(u, torch)
         if "small" in legs:
             out["small_buffers"] = bench_small(u, torch)
+        if "cfg1mib" in legs:
+            out["config_1mib"] = bench_config_1mib(u, torch)
+        if "alu" in legs:
+            out["alu_probe"] = alu_probe()
         if "copy" in legs:
             out["copy_validate"] = bench_copy(u, torch)
         print(json.dumps(out), flush=True)
@@ -451,24 +474,44 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     peaks = measured_peaks()
     peak = float(peaks.get("hbm_gbs") or FALLBACK_HBM_GBS)
-    kernel_time_s = per_buf_ms.sum() / 1e3
-    achieved = bytes_per_step * args.steps / kernel_time_s / 1e9
-    # the ALU roofline over the launches that classify (non-ASCII content)
+    # HBM roofline of validate_kernel: algorithmic bytes (the input, 1 B/B)
+    # per launch over the launch's average event time (1-byte memset + kernel)
+    launch_ms = float(per_buf_ms.mean())
+    achieved = n / (launch_ms / 1e3) / 1e9
+    cfg = json.loads(u.utf8_config_json())
+    traffic = kernel_traffic("validate_kernel", int(cfg["rows"]))
+    # integer-ALU roofline of the launches that classify (non-ASCII content):
+    # ops per byte counted by ncu on the current sources (else the design
+    # count), against the probe's measured ALU-pipe rate x SMs x SM clock
     cls = [i for i, nm in enumerate(names) if not nm.startswith("ascii")]
-    sm_count = int(json.loads(u.utf8_config_json()).get("sm_count", 152))
+    sm_count = int(cfg.get("sm_count", 152))
     sm_mhz = clock_info.get("sm_mhz") or float(peaks.get("sm_max_mhz") or 2070.0)
-    alu_peak = sm_count * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e9  # Gop/s
+    probe = alu_probe() if "alu" in legs else {}
+    alu_rate = min(probe.get(k, 0.0) for k in ("lop3", "prmt", "shf")) if "lop3" in probe else None
+    ops_b = traffic.get("alu_ops_per_byte") if traffic else None
+    alu_roofline = None
     if cls:
         cls_bytes = sum(host[i].size for i in cls) * args.steps
         cls_s = per_buf_ms[:, cls].sum() / 1e3
-        alu_achieved = cls_bytes * ALU_OPS_PER_BYTE / cls_s / 1e9
         cls_gbs = cls_bytes / cls_s / 1e9
-    else:
-        alu_achieved, cls_gbs = None, None
-    traffic = kernel_traffic("validate_kernel", int(json.loads(u.utf8_config_json())["rows"]))
+        ops = ops_b or ALU_OPS_PER_BYTE_DESIGN
+        lanes = alu_rate or 64.0
+        alu_peak = sm_count * lanes * sm_mhz * 1e6 / 1e9  # Gop/s
+        alu_achieved = cls_gbs * ops
+        alu_roofline = {
+            "bound": "alu", "kernel": "validate_kernel (non-ASCII launches)",
+            "achieved": round(alu_achieved, 1), "peak": round(alu_peak, 1), "unit": "Gop/s",
+            "frac": round(alu_achieved / alu_peak, 4),
+            "ops_per_byte": round(ops, 3),
+            "ops_per_byte_source": ("ncu: LOP3+PRMT+SHF executed per byte on these sources"
+                                    if ops_b else "design count (no ncu count on these sources)"),
+            "peak_source": (f"measured: {lanes} ALU ops/clk/SM (probe, slowest of LOP3/PRMT/SHF)"
+                            f" x {sm_count} SMs x {sm_mhz:.0f} MHz median SM clock"
+                            if alu_rate else f"nominal 64 ops/clk/SM x {sm_count} SMs x "
+                                             f"{sm_mhz:.0f} MHz"),
+            "validated_gbs": round(cls_gbs, 1), "probe": probe or None}
     per_variant = {nm: round(host[i].size / (per_buf_ms[:, i].mean() / 1e3) / 1e9, 1)
                    for i, nm in enumerate(names)}
-    cfg = json.loads(u.utf8_config_json())
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
@@ -481,27 +524,17 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                    "launch": cfg},
         "pct_of_hbm_peak": {"measured": round(100 * value / world / peak, 1),
                             "nominal_8000": round(100 * value / world / NOMINAL_HBM_GBS, 1)},
-        "roofline": ({"bound": "alu", "kernel": "validate_kernel (non-ASCII launches)",
-                      "achieved": round(alu_achieved, 1), "peak": round(alu_peak, 1),
-                      "unit": "Gop/s", "frac": round(alu_achieved / alu_peak, 4),
-                      "peak_source": f"derived: {sm_count} SMs x {ALU_LANES_PER_SM} ALU lanes x "
-                                     f"{sm_mhz:.0f} MHz (median SM clock under load)",
-                      "algorithmic_ops_per_byte": round(ALU_OPS_PER_BYTE, 3),
-                      "validated_gbs": round(cls_gbs, 1),
-                      "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
-                      "algorithmic_bytes_per_launch": n}
-                     if cls else
-                     {"bound": "hbm", "kernel": "validate_kernel",
-                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                      "frac": round(achieved / peak, 4),
-                      "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
-                      "algorithmic_bytes_per_launch": n}),
-        "hbm_roofline": {"kernel": "validate_kernel (all launches)",
-                         "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4),
-                         "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback",
-                         "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
-                         "algorithmic_bytes_per_launch": n},
+        "roofline": {"bound": "hbm", "kernel": "validate_kernel",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4),
+                     "peak_source": ("measured (MEASURED_PEAKS.json hbm_gbs, burst copy)"
+                                     if peaks.get("hbm_gbs") else "fallback 6800 GB/s"),
+                     "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                     "algorithmic_bytes_per_launch": n,
+                     "launch_ms": round(launch_ms, 4),
+                     "timing": "CUDA events around each launch (1-byte memset + kernel) on "
+                               "the launching stream, averaged over the timed region"},
+        "alu_roofline": alu_roofline,
         "per_variant_gbs": per_variant,
         "flags": dict(zip(names, flags)),
         "e2e": {"value": round(e2e_value, 1) if e2e_value else None, "unit": "GB/s",
@@ -515,6 +548,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         line["cpu_baseline"] = oracle_baseline(host, names, args.cpu_seconds)
     if world == 1 and "locate" in legs:
         line["locate"] = bench_locate(u, torch, dev, names, stream, flags)
+    if world == 1 and "cfg1mib" in legs:
+        line["config_1mib"] = bench_config_1mib(u, torch)
     if world == 1 and legs & {"batch", "serve", "stream", "copy", "small"}:
         del dev
         torch.cuda.empty_cache()
@@ -797,6 +832,87 @@ def bench_small(u, torch, reps: int = 50) -> dict:
         key = f"{n >> 10}KiB" if n < (1 << 20) else f"{n >> 20}MiB"
         out[key + "_us"] = round(sorted(times)[reps // 2], 2)
         out[key + "_valid"] = int(res.item())
+    return out
+
+
+def bench_config_1mib(u, torch, reps: int = 200) -> dict:
+    """The 1 MiB configuration as configured: one valid 1 MiB buffer of the
+    uniform 1-4 byte mix and seven copies with one injected error each (too
+    short, too long, overlong, too large, surrogate, stray continuation,
+    truncated tail).  Flags against the oracle; p50/p99 latency of
+    utf8_validate_async (CUDA events around the call: 1-byte memset + kernel)
+    and of utf8_validate (host clock around the synchronous call), per
+    buffer over `reps` calls each; and the eight as one utf8_validate_batch
+    call.  L2-hot: the same bytes again and again (1 MiB stays in the 129 MB
+    L2); L2-flushed: a 256 MiB buffer is written between calls."""
+    import oracle
+    import synth
+    bufs, labels = synth.workload_1mib()
+    want = [int(oracle.valid(b)) for b in bufs]
+    dev = [torch.from_numpy(b).cuda() for b in bufs]
+    cat = torch.cat(dev)
+    offs = torch.from_numpy(np.cumsum([0] + [b.size for b in bufs]).astype(np.int64)).cuda()
+    res = torch.empty(1, dtype=torch.uint8, device="cuda")
+    flags8 = torch.empty(len(bufs), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+
+    def pct(v):
+        v = np.asarray(v, np.float64)
+        return {"p50_us": round(float(np.percentile(v, 50)), 2),
+                "p99_us": round(float(np.percentile(v, 99)), 2)}
+
+    def device_us(fn, flushed):
+        times = []
+        with torch.cuda.stream(s):
+            for i in range(reps + 5):
+                if flushed:
+                    flush.fill_(i & 255)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                fn()
+                b.record(s)
+                s.synchronize()
+                if i >= 5:
+                    times.append(a.elapsed_time(b) * 1e3)
+        return times
+
+    def host_us(fn, flushed):
+        times = []
+        with torch.cuda.stream(s):
+            for i in range(reps + 5):
+                if flushed:
+                    flush.fill_(i & 255)
+                    s.synchronize()
+                t = time.perf_counter()
+                fn()
+                dt = time.perf_counter() - t
+                if i >= 5:
+                    times.append(dt * 1e6)
+        return times
+
+    out = {"buffers": labels, "bytes_each": int(bufs[0].size), "reps": reps,
+           "oracle_flags": want}
+    got_async, got_sync = [], []
+    for mode in ("l2_hot", "l2_flushed"):
+        fl = mode == "l2_flushed"
+        a_all, s_all, per = [], [], {}
+        for lab, t in zip(labels, dev):
+            ta = device_us(lambda: u.utf8_validate_async(t, res, stream=s), fl)
+            got_async.append(int(res.item()))
+            box = []
+            ts = host_us(lambda: box.append(u.utf8_validate(t, stream=s)), fl)
+            got_sync.append(int(box[-1]))
+            a_all += ta
+            s_all += ts
+            per[lab] = {"validate_async": pct(ta), "validate": pct(ts)}
+        tb = device_us(lambda: u.utf8_validate_batch(cat, offs, flags8, stream=s), fl)
+        out[mode] = {"validate_async_all_buffers": pct(a_all), "validate_all_buffers": pct(s_all),
+                     "per_buffer": per,
+                     "batch_of_8": {**pct(tb), "flags": flags8.cpu().numpy().tolist()}}
+    out["flags_match_oracle"] = (got_async == want * 2 and got_sync == want * 2
+                                 and out["l2_hot"]["batch_of_8"]["flags"] == want
+                                 and out["l2_flushed"]["batch_of_8"]["flags"] == want)
     return out
 
 

@@ -247,12 +247,17 @@ void utf8_stream_destroy(utf8_stream* s);
  * fixed footprint.  The paper has no counterpart; it is a packaging of the
  * same kernel.  The input (host memory, len <= 32 MiB; longer inputs are
  * rejected with UTF8_ERR_BUDGET) is staged through a fixed 32 MiB + 4 KiB
- * array compiled into the library, which every GPU that loads the library
- * holds until exit.  A device's first call looks up that array's device
- * address; make it before any stream capture.  All calls share the array:
- * calls whose work overlaps on the GPU race on it (serialise them).
- * Synchronous; returns true iff valid, false with utf8_last_error() set
- * otherwise.
+ * array compiled into the library.  Under CUDA's lazy module loading (the
+ * default) a device gets its copy of the array, and the validation kernels,
+ * when the first call on that device loads them, and keeps them until exit:
+ * make one call on each device (len 0 is enough; host_data may be NULL)
+ * before reserving the device's memory, and before any stream capture
+ * begins.  A first call that fails (UTF8_ERR_CUDA, e.g. no memory left to
+ * load the module) is retried by the next one.  All calls share the array:
+ * calls whose work overlaps on the GPU race on it (serialise them); the array
+ * keeps the previous call's bytes, which never affect a later result.
+ * Synchronous (waits for `stream`); returns true iff valid, false with
+ * utf8_last_error() set otherwise.
  */
 bool utf8_validate_host_noalloc(const uint8_t* host_data, size_t len, cudaStream_t stream);
 

@@ -15,6 +15,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libutf8gpu.so")
+# the integer-pipe throughput probe (bench.py's ALU roofline peak), kept
+# out of the validator library
+PROBE_SRC = os.path.join(HERE, "probe", "alu_probe.cu")
+PROBE_LIB = os.path.join(BUILD, "libaluprobe.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -72,6 +76,21 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
     return LIB
+
+
+def build_probe(force: bool = False) -> str:
+    if (not force and os.path.exists(PROBE_LIB)
+            and os.path.getmtime(PROBE_SRC) <= os.path.getmtime(PROBE_LIB)):
+        return PROBE_LIB
+    os.makedirs(BUILD, exist_ok=True)
+    tmp = f"{PROBE_LIB}.{os.getpid()}.tmp"
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+           "-cudart", "static", PROBE_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {PROBE_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
 
 
 if __name__ == "__main__":

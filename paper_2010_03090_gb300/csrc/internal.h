@@ -31,6 +31,8 @@ cudaError_t launch_validate_tiles(const uint8_t* data, uint64_t n, uint64_t t_be
                                   uint64_t t_end, uint8_t* out_valid, const LaunchCfg& cfg,
                                   int sm_count, cudaStream_t st);
 uint64_t tile_bytes(const LaunchCfg& cfg);
+// Loads every form of the single-buffer kernel (validate.cu).
+cudaError_t preload_validate_kernels();
 
 // Early exit of the single-buffer validation kernel (utf8_set_early_exit):
 // process-wide, initially UTF8GPU_EARLY_EXIT (non-zero = on; off if unset).

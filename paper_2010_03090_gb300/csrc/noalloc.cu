@@ -11,16 +11,21 @@
 // so it never calls cudaMalloc, cudaFree, cudaHostAlloc or any allocator.
 //
 // The array (result byte + halo room + kNoAllocMaxBytes of input) is a
-// file-scope __device__ variable: every GPU that loads the library holds it
-// until the process exits.  Its device address is looked up once per device
-// with cudaGetSymbolAddress (a host-side mention of the array names a host
-// stand-in, not device memory).  Every call shares the array, so calls whose
-// work overlaps on the GPU (other threads, other streams) race on it; the
-// result byte is reset to 1 at the start of every call.
+// file-scope __device__ variable.  Under CUDA's lazy module loading (the
+// default) a device gets its copy when this file's module is loaded there,
+// which the first call on that device does, and keeps it until the process
+// exits.  That first call (len 0 is enough) also loads the validation
+// kernels, so a caller that reserves its GPU memory up front makes it on
+// every device before reserving.  Its device address is looked up once per
+// device with cudaGetSymbolAddress (a host-side mention of the array names a
+// host stand-in, not device memory); a set-up that fails (for example out of
+// memory while the module loads) is retried by the next call.  Every call
+// shares the array, so calls whose work overlaps on the GPU (other threads,
+// other streams) race on it; the result byte is reset to 1 at the start of
+// every call.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <functional>
 #include <mutex>
 
 #include "internal.h"
@@ -41,8 +46,8 @@ static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocHead + kNoAll
 constexpr int kMaxDevices = 64;
 
 struct NoAllocDevice {
-  std::once_flag once;
-  cudaError_t err = cudaSuccess;
+  std::mutex mu;
+  bool ready = false;          // set-up done (only ever goes from false to true)
   uint8_t* scratch = nullptr;  // device address of g_noalloc_scratch
   int sm_count = 0;
   LaunchCfg cfg;
@@ -50,12 +55,29 @@ struct NoAllocDevice {
 
 NoAllocDevice g_na[kMaxDevices];
 
-// Runs on a device's first call, with that device current.
-void setup(NoAllocDevice& d, int dev) {
-  d.err = cudaGetSymbolAddress(reinterpret_cast<void**>(&d.scratch), g_noalloc_scratch);
-  if (d.err == cudaSuccess)
-    d.err = cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev);
-  if (d.err == cudaSuccess) clamp_to_occupancy(d.cfg);  // defaults, no tuning cache
+// Per-device set-up, with that device current: loads this module (and with it
+// the array) and the validation kernels, and looks up the array's address.
+// Returns false, leaving `ready` unset so that the next call tries again, if
+// any step fails.
+bool setup(NoAllocDevice& d, int dev) {
+  std::lock_guard<std::mutex> lock(d.mu);
+  if (d.ready) return true;
+  uint8_t* scratch = nullptr;
+  int sms = 0;
+  cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&scratch), g_noalloc_scratch);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = preload_validate_kernels();
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // do not leave the failure to the caller's next CUDA call
+    return false;
+  }
+  LaunchCfg cfg;
+  clamp_to_occupancy(cfg);  // defaults, no tuning cache
+  d.scratch = scratch;
+  d.sm_count = sms;
+  d.cfg = cfg;
+  d.ready = true;
+  return true;
 }
 
 }  // namespace
@@ -66,8 +88,7 @@ using namespace utf8gpu;
 
 extern "C" bool utf8_validate_host_noalloc(const uint8_t* host_data, size_t len,
                                            cudaStream_t stream) {
-  if (len == 0) return set_thread_status(UTF8_OK), true;
-  if (host_data == nullptr) return set_thread_status(UTF8_ERR_INVALID_ARG), false;
+  if (host_data == nullptr && len > 0) return set_thread_status(UTF8_ERR_INVALID_ARG), false;
   if (len > kNoAllocMaxBytes) return set_thread_status(UTF8_ERR_BUDGET), false;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -75,8 +96,9 @@ extern "C" bool utf8_validate_host_noalloc(const uint8_t* host_data, size_t len,
     return set_thread_status(UTF8_ERR_CUDA), false;
   }
   NoAllocDevice& d = g_na[dev];
-  std::call_once(d.once, setup, std::ref(d), dev);
-  if (d.err != cudaSuccess) return set_thread_status(UTF8_ERR_CUDA), false;
+  // set-up first, so that a len 0 call prepares the device
+  if (!setup(d, dev)) return set_thread_status(UTF8_ERR_CUDA), false;
+  if (len == 0) return set_thread_status(UTF8_OK), true;
 
   uint8_t* result = d.scratch;               // starts each call at 1 (valid)
   uint8_t* staged = d.scratch + kNoAllocHead;

@@ -156,6 +156,20 @@ static int validate_fit() {
   return n > 0 ? n : 1;
 }
 
+// Loads every form of validate_kernel that launch_validate_tiles can launch
+// (under lazy module loading a kernel is otherwise loaded at its first
+// launch, which may then need device memory).
+cudaError_t preload_validate_kernels() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, validate_kernel<2, false>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, validate_kernel<2, true>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, validate_kernel<4, false>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, validate_kernel<4, true>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, validate_kernel<8, false>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, validate_kernel<8, true>);
+  return e;
+}
+
 int validate_blocks_per_sm(int rows) {
   switch (rows) {
     case 2: return validate_fit<2>();

@@ -149,6 +149,29 @@ def test_every_4_byte_string_count_by_lead():
     assert got[0xC0:].sum() == oracle.count_valid(4, lead_min=0xC0)
 
 
+def test_every_4_byte_string_with_a_lead_flag_by_flag():
+    """Every 4-byte string whose first byte is a lead (0xC0..0xFF), flag by
+    flag against the oracle on the same bytes.  (A first byte below 0xC0 is
+    ASCII, whose string is valid iff its last three bytes are, a case the
+    every-3-byte-string test covers flag by flag, or a continuation, which is
+    always invalid: the per-lead counts above check both.)"""
+    per = 1 << 24
+    tails = np.arange(per, dtype=np.uint32).view(np.uint8).reshape(per, 4)[:, :3]
+    host = np.empty((per, 4), dtype=np.uint8)
+    host[:, 1:] = tails
+    offsets = np.arange(0, 4 * per + 1, 4, dtype=np.int64)
+    o = torch.from_numpy(offsets).cuda()
+    threads = max(len(os.sched_getaffinity(0)), 1)
+    for b in range(0xC0, 0x100):
+        host[:, 0] = b
+        flags = u.utf8_validate_batch(dev(host.reshape(-1)), o).cpu().numpy()
+        want = oracle.valid_batch(host.reshape(-1), offsets, threads=threads)
+        if not np.array_equal(flags, want):
+            bad = np.flatnonzero(flags != want)[:5]
+            pytest.fail(f"lead {b:#04x}: {bad.size} strings differ, e.g. "
+                        f"{[bytes(host[i]).hex() for i in bad]}")
+
+
 # --------------------------------------------------------------------------
 # single-buffer API: every length and alignment, errors at tile boundaries
 # --------------------------------------------------------------------------
