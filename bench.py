@@ -42,9 +42,14 @@ NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6800.0
 METRIC = "validated GB/s"
 # Integer ALU-pipe operations (LOP3, PRMT, SHF) per byte of non-ASCII text,
-# as the kernel's design counts them (used only when no ncu count taken on
-# the current kernel sources is on record in profiles/traffic.json).
-ALU_OPS_PER_BYTE_DESIGN = (34 + 2 / 16) / 8
+# as the kernel's design counts them for one 8-byte interleaved pair:
+# selectors 7 (one right shift, 3 bit selects, 3 half-word shifts), table
+# lookups 10 and their AND 2, the checks 8 (per word: two funnel shifts, the
+# expectation mask and the error XOR) and the error fold 1: 28 (8 SHF, 10
+# PRMT, 10 LOP3), plus the tile's all-ASCII test on its first row, 2 per 16
+# pairs.  Used only when no ncu count taken on the current kernel sources is
+# on record in profiles/traffic.json.
+ALU_OPS_PER_BYTE_DESIGN = (28 + 2 / 16) / 8
 WORKLOAD = ("single 1 GiB buffers: 5 seeded content variants (ascii, latin, cjk, emoji, "
             "uniform 1-4 byte) + a truncated-tail copy of each = 10 GiB per step")
 
@@ -210,29 +215,33 @@ def source_hash(files=("lookup.cuh", "tiles.cuh", "validate.cu")) -> str:
     return h.hexdigest()[:16]
 
 
-def alu_probe(blocks_per_sm: int = 8, iters: int = 20000) -> dict:
+def alu_probe(sm_mhz: float, blocks_per_sm: int = 8, iters: int = 20000) -> dict:
     """Operations per clock per SM of the integer pipes (LOP3, PRMT, SHF on
     the ALU pipe; IMAD on the FMA pipe; PRMT and IMAD mixed), measured now by
-    the probe kernel: the denominator of the integer-ALU roofline."""
+    the probe kernel (CUDA events, full grid, independent chains) at the SM
+    clock sampled during the timed region: the denominator of the
+    integer-ALU roofline."""
     import ctypes
     from paper_2010_03090_gb300 import build as cuda_build
     L = ctypes.CDLL(cuda_build.build_probe())
     L.alu_probe_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint,
                                 ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
-                                ctypes.POINTER(ctypes.c_int)]
+                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
     L.alu_probe_run.restype = ctypes.c_int
-    out = {}
+    out, ticks = {}, {}
     for op, name in enumerate(("lop3", "prmt", "shf", "imad", "prmt+imad")):
-        ops, sms = ctypes.c_double(), ctypes.c_int()
+        ops, sms, ms = ctypes.c_double(), ctypes.c_int(), ctypes.c_float()
         cyc = np.zeros(4096, np.int64)
         for _ in range(2):  # the first run warms up
             rc = L.alu_probe_run(op, blocks_per_sm, iters, cyc.ctypes.data, ctypes.byref(ops),
-                                 ctypes.byref(sms))
+                                 ctypes.byref(sms), ctypes.byref(ms))
             if rc != 0:
                 return {"error": f"probe failed: CUDA error {rc}"}
-        spans = cyc[: blocks_per_sm * sms.value]
-        out[name] = round(ops.value * blocks_per_sm / float(np.median(spans)), 2)
-    out["unit"] = "thread operations per clock per SM (median block cycle span)"
+        per_sm = ops.value * blocks_per_sm
+        out[name] = round(per_sm / (ms.value * 1e-3 * sm_mhz * 1e6), 2)
+        ticks[name] = round(per_sm / float(np.median(cyc[: blocks_per_sm * sms.value])), 2)
+    out["unit"] = f"thread operations per SM clock (CUDA events, at {sm_mhz:.0f} MHz)"
+    out["per_clock64_tick"] = ticks
     return out
 
 
@@ -390,7 +399,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         if "cfg1mib" in legs:
             out["config_1mib"] = bench_config_1mib(u, torch)
         if "alu" in legs:
-            out["alu_probe"] = alu_probe()
+            out["alu_probe"] = alu_probe(float(measured_peaks().get("sm_max_mhz") or 2070.0))
         if "copy" in legs:
             out["copy_validate"] = bench_copy(u, torch)
         print(json.dumps(out), flush=True)
@@ -486,7 +495,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     cls = [i for i, nm in enumerate(names) if not nm.startswith("ascii")]
     sm_count = int(cfg.get("sm_count", 152))
     sm_mhz = clock_info.get("sm_mhz") or float(peaks.get("sm_max_mhz") or 2070.0)
-    probe = alu_probe() if "alu" in legs else {}
+    probe = alu_probe(sm_mhz) if "alu" in legs else {}
     alu_rate = min(probe.get(k, 0.0) for k in ("lop3", "prmt", "shf")) if "lop3" in probe else None
     ops_b = traffic.get("alu_ops_per_byte") if traffic else None
     alu_roofline = None

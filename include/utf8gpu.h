@@ -262,16 +262,25 @@ void utf8_stream_destroy(utf8_stream* s);
 bool utf8_validate_host_noalloc(const uint8_t* host_data, size_t len, cudaStream_t stream);
 
 /*
- * Debug view of the classification (Fig. 1 and Section 6.2) of one buffer:
- * for each position i in 0 .. len+2 (the buffer followed by its three zero
- * padding bytes) writes special_cases[i] = byte_1_high & byte_1_low &
- * byte_2_high of (data[i-1], data[i]) and must23[i] = 0x80 where two
- * continuations are expected (data[i-2] >= 0xE0 or data[i-3] >= 0xF0), with
- * zeros before the buffer.  out_special, out_must23: device uint8[len + 3].
- * Uses the same device code as the validators.  Asynchronous.
+ * Debug view of the classification (Section 6.1, Fig. 1, Table 7; Section
+ * 6.2) of one buffer, from the device code the validators run: for each
+ * position i in 0 .. len+2 (the buffer followed by its three zero padding
+ * bytes, zeros before it) writes
+ *   out_special[i] = the second-byte rows of Table 7 that (data[i-1], data[i])
+ *     matches, through the three AND-ed nibble tables: bit 0 overlong
+ *     2-byte (C0, C1), bit 1 overlong 3-byte (E0 80..9F), bit 2 surrogate
+ *     (ED A0..BF), bit 3 too large (F4..FF 90..BF), bit 4 overlong 4-byte or
+ *     too large (F0 or F5..FF, then 80..8F).  Where data[i-1] is ASCII and
+ *     data[i] a continuation (an error in any case) the bits are unspecified;
+ *   out_cont[i] = bit 0: a continuation is expected at i: data[i-1] >= 0xC0
+ *     (TOO_SHORT), or exactly one of data[i-2] >= 0xE0 and data[i-3] >= 0xF0
+ *     (must_be_2_3; both hold only where a lead follows a 4-byte lead, an
+ *     error that position i-2 shows); bit 1: data[i] is a continuation.
+ * Position i is an error iff out_special[i] != 0 or its two cont bits differ.
+ * out_special, out_cont: device uint8[len + 3].  Asynchronous.
  */
 int utf8_classify_debug(const uint8_t* data, size_t len, uint8_t* out_special,
-                        uint8_t* out_must23, cudaStream_t stream);
+                        uint8_t* out_cont, cudaStream_t stream);
 
 /*
  * Continuous-batching server.  Requests are device-resident buffers submitted

@@ -352,14 +352,15 @@ def utf8_stream_destroy(h) -> None:
 
 
 def utf8_classify_debug(data, stream=None):
-    """Per-position special_cases and must_be_2_3 bytes (len + 3 each)."""
+    """Per-position special-row bits and continuation bits (len + 3 each):
+    see utf8_classify_debug in utf8gpu.h."""
     import torch
     p, n = _dev(data, "uint8", "data")
     sc = torch.empty(n + 3, dtype=torch.uint8, device=data.device)
-    m = torch.empty(n + 3, dtype=torch.uint8, device=data.device)
-    _check(lib().utf8_classify_debug(p or None, n, sc.data_ptr(), m.data_ptr(), _stream(stream)),
-           "utf8_classify_debug")
-    return sc, m
+    cont = torch.empty(n + 3, dtype=torch.uint8, device=data.device)
+    _check(lib().utf8_classify_debug(p or None, n, sc.data_ptr(), cont.data_ptr(),
+                                     _stream(stream)), "utf8_classify_debug")
+    return sc, cont
 
 
 def utf8_last_error() -> int:

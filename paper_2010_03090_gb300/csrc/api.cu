@@ -376,15 +376,15 @@ int utf8_copy_validate(uint8_t* dst, const uint8_t* src, size_t len, uint8_t* ou
 }
 
 int utf8_classify_debug(const uint8_t* data, size_t len, uint8_t* out_special,
-                        uint8_t* out_must23, cudaStream_t stream) {
-  if (out_special == nullptr || out_must23 == nullptr || (data == nullptr && len > 0))
+                        uint8_t* out_cont, cudaStream_t stream) {
+  if (out_special == nullptr || out_cont == nullptr || (data == nullptr && len > 0))
     return set_status(UTF8_ERR_INVALID_ARG);
   DeviceState* d = device();
   if (!d) return UTF8_ERR_CUDA;
-  if (!is_device_memory(out_special) || !is_device_memory(out_must23) ||
+  if (!is_device_memory(out_special) || !is_device_memory(out_cont) ||
       (len > 0 && !is_device_memory(data)))
     return set_status(UTF8_ERR_INVALID_ARG);
-  return cuda_status(launch_classify_debug(data, len, out_special, out_must23, stream));
+  return cuda_status(launch_classify_debug(data, len, out_special, out_cont, stream));
 }
 
 int utf8_last_error(void) { return tl_status; }

@@ -40,7 +40,7 @@ bool early_exit_enabled();
 int set_early_exit(int enable);  // returns the previous setting (0 or 1)
 
 cudaError_t launch_classify_debug(const uint8_t* data, uint64_t n, uint8_t* out_special,
-                                  uint8_t* out_must23, cudaStream_t st);
+                                  uint8_t* out_cont, cudaStream_t st);
 
 // One independent buffer of a segment batch (segments.cu).
 struct SegmentDesc {

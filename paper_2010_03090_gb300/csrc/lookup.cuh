@@ -5,66 +5,100 @@
 // the current byte, AND-ed together (Section 6.1, Fig. 1, Table 7); it then
 // compares bit 7 (two continuations in a row) with the positions where a
 // 3- or 4-byte lead two or three bytes back requires one (Section 6.2), and
-// pads the end of the stream with ASCII zeros (Section 6.3).  Any non-zero
-// byte of  (byte_1_high & byte_1_low & byte_2_high) ^ must_be_2_3  is an error.
+// pads the end of the stream with ASCII zeros (Section 6.3).
 //
 // On the GPU the 16-byte shuffle of the paper (vpshufb / tbl) becomes the
-// byte-permute instruction `prmt`, four lookups per 32-bit word, with these
-// design points (all exact; an exhaustive test over every byte pair and every
-// (prev3, prev2) pair checks them against the tables):
+// byte-permute instruction `prmt`, four lookups per 32-bit word.  prmt takes
+// four 4-bit selectors; a selector with bit 3 set does not look up an entry
+// but replicates the sign bit of byte (selector & 7).  With the complemented
+// high nibble (15 - n) as selector, the eight non-ASCII high nibbles 8..F
+// index an ordinary 8-byte table and every ASCII byte comes out as 0x00 or
+// 0xFF, set by the sign bits of that table.  The classification is arranged
+// so that those sign-mode values are the right ones, with no per-byte
+// correction for ASCII:
 //
-//  * Nibble selectors.  prmt takes four 4-bit selectors packed in 16 bits.
-//    In the streaming kernels two rows of a tile are processed side by side
-//    (lut_interleaved): interleaving their bytes lets one shift and one mask
-//    pack the selectors of eight bytes.
-//  * 16 entries from an 8-byte prmt table.  A selector nibble with bit 3 set
-//    makes prmt replicate the sign bit of the selected byte.  With the
-//    complemented high nibble (15 - n) the eight non-ASCII leads 8..F index
-//    an ordinary 8-byte table; ASCII bytes fall into sign mode and are
-//    replaced afterwards by the table's constant for 0..7 (0x02 for
-//    byte_1_high, 0x01 for byte_2_high), under a mask of the bytes' sign bits.
-//  * byte_1_low has bit 7 set in all 16 entries, so a lookup through the
-//    plain low nibble (entries 0..7, sign mode gives 0xFF for 8..F) AND-ed
-//    with a lookup through the complemented low nibble (entries 8..F, 0xFF for
-//    0..7) gives the table exactly.
+//  * The five second-byte rows of Table 7 (OVERLONG_2, OVERLONG_3,
+//    SURROGATE, TOO_LARGE, OVERLONG_4 | TOO_LARGE_1000) keep the paper's
+//    three AND-ed tables, one bit each.  byte_1_high has bit 7 in every
+//    non-ASCII entry, so an ASCII previous byte reads 0xFF: it then matches a
+//    special row only together with a continuation after it, a pair that is
+//    invalid anyway.  byte_2_high has no bit 7 anywhere, so an ASCII current
+//    byte reads 0x00 and matches nothing.
+//  * The other three rows of Table 7 (TOO_SHORT: a lead not followed by a
+//    continuation; TOO_LONG: a continuation after ASCII; TWO_CONTS, checked
+//    against must_be_2_3) all say one thing: byte i is a continuation exactly
+//    when one is expected there, i.e. when byte i-1 >= 0xC0, byte i-2 >= 0xE0
+//    or byte i-3 >= 0xF0.  Section 6.2 builds the last two terms
+//    (must_be_2_3); the first is the TOO_SHORT / TOO_LONG pair.  Here the
+//    whole condition is one bit (0x40): the current side's table sets it for
+//    continuations, the previous side's tables set it for every byte, and the
+//    expectation is XOR-ed onto it, so bit 6 of a position is non-zero iff
+//    "is a continuation" differs from "expects one".  The expectation comes
+//    from a fourth lookup of lead flags (bit 6: >= 0xC0, bit 5: >= 0xE0,
+//    bit 4: >= 0xF0), moved onto bit 6 from one, two and three bytes back.
+//  * byte_1_low has bit 7 in all 16 entries, so a lookup through the plain
+//    low nibble (entries 0..7, sign mode gives 0xFF for 8..F) AND-ed with a
+//    lookup through the complemented low nibble (entries 8..F, 0xFF for 0..7)
+//    gives the table exactly.
 //  * The previous-byte lookups are computed on the current bytes, then moved
 //    to the next position by a funnel shift (the paper's prev<1>), so each
 //    byte is looked up once.
-//  * must_be_2_3: one more high-nibble lookup gives bit 6 = (byte >= 0xE0)
-//    and bit 5 = (byte >= 0xF0); shifts move bit 6 of the byte two back and
-//    bit 5 of the byte three back onto bit 7, and their OR under 0x80808080
-//    is the paper's (prev2 >= 0xE0) | (prev3 >= 0xF0) mask.
 //
-// Bit assignment: the one printed in Table 8 (TOO_SHORT 0x01, TOO_LONG 0x02,
-// OVERLONG_3 0x04, TOO_LARGE 0x08, SURROGATE 0x10, OVERLONG_2 0x20,
-// OVERLONG_4 | TOO_LARGE_1000 0x40, TWO_CONTS 0x80).
+// A position is an error iff its byte  ((prev side of byte i-1) & (current
+// side of byte i)) ^ (expectation of byte i)  is non-zero; it has no bits
+// outside 0x5F.  This decides exactly the paper's boolean: an exhaustive test
+// checks the tables against Table 7's rows (the special bits equal the
+// paper's wherever the previous byte is not ASCII) and the whole check
+// against the oracle on every class string of up to seven bytes.
 #pragma once
 #include <stdint.h>
 
 namespace utf8gpu {
 
 // ---------------------------------------------------------------------------
-// The three tables of Section 6.1, entry n = nibble value n (Table 8 values).
+// Bits of a position's classification byte.
 // ---------------------------------------------------------------------------
-constexpr uint8_t kByte1High[16] = {
-    0x02, 0x02, 0x02, 0x02, 0x02, 0x02, 0x02, 0x02,   // 0xxx: ASCII -> TOO_LONG
-    0x80, 0x80, 0x80, 0x80,                           // 10xx: continuation
-    0x21,                                             // 1100: TOO_SHORT | OVERLONG_2
-    0x01,                                             // 1101: TOO_SHORT
-    0x15,                                             // 1110: TOO_SHORT | OVERLONG_3 | SURROGATE
-    0x49};                                            // 1111: TOO_SHORT | TOO_LARGE | 0x40
-constexpr uint8_t kByte1Low[16] = {
-    0xE7, 0xA3, 0x83, 0x83, 0x8B, 0xCB, 0xCB, 0xCB,
-    0xCB, 0xCB, 0xCB, 0xCB, 0xCB, 0xDB, 0xCB, 0xCB};
-constexpr uint8_t kByte2High[16] = {
-    0x01, 0x01, 0x01, 0x01, 0x01, 0x01, 0x01, 0x01,   // ASCII: TOO_SHORT
-    0xE6, 0xAE, 0xBA, 0xBA,                           // continuations
-    0x01, 0x01, 0x01, 0x01};                          // leads: TOO_SHORT
-// must_be_2_3 flags per high nibble: bit 6 = (byte >= 0xE0), bit 5 = (byte >= 0xF0)
-constexpr uint8_t kLeadFlags[16] = {
-    0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0x40, 0x60};
+constexpr uint8_t kOverlong2 = 0x01;  // C0, C1 + continuation            (Table 7: OVERLONG_2)
+constexpr uint8_t kOverlong3 = 0x02;  // E0 + 80..9F                      (OVERLONG_3)
+constexpr uint8_t kSurrogate = 0x04;  // ED + A0..BF                      (SURROGATE)
+constexpr uint8_t kTooLarge = 0x08;   // F4..FF + 90..BF                  (TOO_LARGE)
+constexpr uint8_t kOverlong4 = 0x10;  // F0, F5..FF + 80..8F  (OVERLONG_4 | TOO_LARGE_1000)
+constexpr uint8_t kCont = 0x40;       // continuation (current side; every previous byte)
+constexpr uint8_t kSpecialBits = 0x1F;
+constexpr uint32_t kContBits = 0x40404040u;
+// lead flags (current byte): kCont = >= 0xC0, 0x20 = >= 0xE0, 0x10 = >= 0xF0
+constexpr uint8_t kGeE0 = 0x20, kGeF0 = 0x10;
 
-constexpr uint32_t kTwoConts = 0x80808080u;
+// The tables, entry n = nibble value n.
+// byte_1_high: entries 0..7 are what prmt's sign mode produces for ASCII.
+constexpr uint8_t kByte1High[16] = {
+    0xFF, 0xFF, 0xFF, 0xFF, 0xFF, 0xFF, 0xFF, 0xFF,    // ASCII (sign mode)
+    0xC0, 0xC0, 0xC0, 0xC0,                            // continuation
+    0xC0 | kOverlong2,                                 // 1100
+    0xC0,                                              // 1101
+    0xC0 | kOverlong3 | kSurrogate,                    // 1110
+    0xC0 | kTooLarge | kOverlong4};                    // 1111
+constexpr uint8_t kByte1Low[16] = {
+    0xC0 | kOverlong2 | kOverlong3 | kOverlong4,       // 0
+    0xC0 | kOverlong2,                                 // 1
+    0xC0, 0xC0,                                        // 2, 3
+    0xC0 | kTooLarge,                                  // 4
+    0xC0 | kTooLarge | kOverlong4, 0xC0 | kTooLarge | kOverlong4,
+    0xC0 | kTooLarge | kOverlong4, 0xC0 | kTooLarge | kOverlong4,
+    0xC0 | kTooLarge | kOverlong4, 0xC0 | kTooLarge | kOverlong4,
+    0xC0 | kTooLarge | kOverlong4, 0xC0 | kTooLarge | kOverlong4,    // 5..C
+    0xC0 | kTooLarge | kOverlong4 | kSurrogate,                      // D
+    0xC0 | kTooLarge | kOverlong4, 0xC0 | kTooLarge | kOverlong4};   // E, F
+constexpr uint8_t kByte2High[16] = {
+    0, 0, 0, 0, 0, 0, 0, 0,                                          // ASCII (sign mode)
+    kCont | kOverlong2 | kOverlong3 | kOverlong4,                    // 1000
+    kCont | kOverlong2 | kOverlong3 | kTooLarge,                     // 1001
+    kCont | kOverlong2 | kSurrogate | kTooLarge,                     // 1010
+    kCont | kOverlong2 | kSurrogate | kTooLarge,                     // 1011
+    0, 0, 0, 0};                                                     // leads
+constexpr uint8_t kLeadFlags[16] = {
+    0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0,
+    kCont, kCont, kCont | kGeE0, kCont | kGeE0 | kGeF0};
 
 constexpr uint32_t pack4(uint8_t b0, uint8_t b1, uint8_t b2, uint8_t b3) {
   return (uint32_t)b0 | ((uint32_t)b1 << 8) | ((uint32_t)b2 << 16) | ((uint32_t)b3 << 24);
@@ -77,21 +111,34 @@ constexpr uint32_t lowHalf(const uint8_t* t, int w) {
 constexpr uint32_t highHalfReversed(const uint8_t* t, int w) {
   return pack4(t[15 - 4 * w], t[14 - 4 * w], t[13 - 4 * w], t[12 - 4 * w]);
 }
+constexpr bool allSigns(const uint8_t* t, int from, int to, bool set) {
+  return from == to ? true : (((t[from] & 0x80) != 0) == set && allSigns(t, from + 1, to, set));
+}
+constexpr bool allEqual(const uint8_t* t, int from, int to, uint8_t v) {
+  return from == to ? true : (t[from] == v && allEqual(t, from + 1, to, v));
+}
 
 constexpr uint32_t kB1H_R0 = highHalfReversed(kByte1High, 0), kB1H_R1 = highHalfReversed(kByte1High, 1);
 constexpr uint32_t kB2H_R0 = highHalfReversed(kByte2High, 0), kB2H_R1 = highHalfReversed(kByte2High, 1);
 constexpr uint32_t kFlg_R0 = highHalfReversed(kLeadFlags, 0), kFlg_R1 = highHalfReversed(kLeadFlags, 1);
 constexpr uint32_t kB1L_L0 = lowHalf(kByte1Low, 0), kB1L_L1 = lowHalf(kByte1Low, 1);
 constexpr uint32_t kB1L_R0 = highHalfReversed(kByte1Low, 0), kB1L_R1 = highHalfReversed(kByte1Low, 1);
-constexpr uint32_t kAsciiB1H = 0x01010101u * kByte1High[0];
-constexpr uint32_t kAsciiB2H = 0x01010101u * kByte2High[0];
+// prev_side of four zero bytes: byte_1_high of ASCII (0xFF) & byte_1_low[0]
+constexpr uint32_t kZeroPrevSide = 0x01010101u * kByte1Low[0];
 
-static_assert(kFlg_R1 == 0 && (kFlg_R0 & 0x80808080u) == 0,
-              "lead flags must stay clear of bit 7 so ASCII sign-mode lookups give 0");
-static_assert((kB1L_L0 & kB1L_L1 & kB1L_R0 & kB1L_R1 & 0x80808080u) == 0x80808080u,
-              "byte_1_low must have bit 7 in every entry for the AND merge");
-static_assert((kB1L_L0 & kB1L_L1 & kB1L_R0 & kB1L_R1 & kAsciiB1H) == kAsciiB1H,
-              "for an ASCII previous byte, byte_1_high & byte_1_low is byte_1_high's 0x02");
+// What the sign mode produces for ASCII bytes is what the tables say for them.
+static_assert(allSigns(kByte1High, 8, 16, true) && allEqual(kByte1High, 0, 8, 0xFF),
+              "byte_1_high: sign bits set for 8..F, so ASCII reads 0xFF");
+static_assert(allSigns(kByte2High, 8, 16, false) && allEqual(kByte2High, 0, 8, 0),
+              "byte_2_high: sign bits clear for 8..F, so ASCII reads 0");
+static_assert(allSigns(kLeadFlags, 8, 16, false) && allEqual(kLeadFlags, 0, 8, 0),
+              "lead flags: sign bits clear for 8..F, so ASCII reads 0");
+static_assert(allSigns(kByte1Low, 0, 16, true),
+              "byte_1_low: bit 7 in every entry, so the two half lookups AND to the table");
+// Every previous byte carries the continuation bit; only the current side's
+// continuations and the expectation decide it.
+static_assert((kB1L_L0 & kB1L_L1 & kB1L_R0 & kB1L_R1 & kB1H_R0 & kB1H_R1 & kContBits) == kContBits,
+              "the previous side has bit 6 in every entry");
 
 // ---------------------------------------------------------------------------
 // primitives
@@ -117,25 +164,21 @@ __device__ __forceinline__ uint32_t bit_select_not(uint32_t a, uint32_t b, uint3
   return d;
 }
 
-// Lookup results for one 32-bit word (four consecutive bytes).
+// Lookup results for one 32-bit word (four bytes).
 struct WordLut {
   uint32_t prev_side;  // byte_1_high[hi] & byte_1_low[lo] of each byte (used as prev1)
   uint32_t cur_side;   // byte_2_high[hi] of each byte
-  uint32_t flags;      // bit 6: byte >= 0xE0, bit 5: byte >= 0xF0
+  uint32_t flags;      // lead flags of each byte (0x40: >= 0xC0, 0x20: >= 0xE0, 0x10: >= 0xF0)
 };
 
-// Table lookups for one word, given its packed selectors.
-//   nonascii : 0xFF in each byte whose byte value has its msb set
+// Table lookups for one word, given its packed selectors:
 //   hi_c     : complemented high nibbles in bits 0..15
 //   lo, lo_c : low nibbles and their complements in bits 0..15
-__device__ __forceinline__ WordLut lut_from_selectors(uint32_t nonascii, uint32_t hi_c, uint32_t lo,
-                                                      uint32_t lo_c) {
-  const uint32_t b1h = prmt(kB1H_R0, kB1H_R1, hi_c);
-  const uint32_t b2h = prmt(kB2H_R0, kB2H_R1, hi_c);
-  const uint32_t b1l = prmt(kB1L_L0, kB1L_L1, lo) & prmt(kB1L_R0, kB1L_R1, lo_c);
+__device__ __forceinline__ WordLut lut_from_selectors(uint32_t hi_c, uint32_t lo, uint32_t lo_c) {
   WordLut r;
-  r.prev_side = ((b1h & b1l) & nonascii) | (kAsciiB1H & ~nonascii);
-  r.cur_side = (b2h & nonascii) | (kAsciiB2H & ~nonascii);
+  r.prev_side = prmt(kB1H_R0, kB1H_R1, hi_c) & prmt(kB1L_L0, kB1L_L1, lo) &
+                prmt(kB1L_R0, kB1L_R1, lo_c);
+  r.cur_side = prmt(kB2H_R0, kB2H_R1, hi_c);
   r.flags = prmt(kFlg_R0, kFlg_R1, hi_c);
   return r;
 }
@@ -150,8 +193,8 @@ __device__ __forceinline__ void lut_pair(uint32_t c, uint32_t d, WordLut& lc, Wo
   const uint32_t hi_c = bit_select_not(u >> 4, v, lo_mask);
   const uint32_t lo = bit_select(u, v << 4, lo_mask);
   const uint32_t lo_c = bit_select_not(u, v << 4, lo_mask);
-  lc = lut_from_selectors(prmt(c, 0, 0xBA98), hi_c, lo, lo_c);
-  ld = lut_from_selectors(prmt(d, 0, 0xBA98), hi_c >> 16, lo >> 16, lo_c >> 16);
+  lc = lut_from_selectors(hi_c, lo, lo_c);
+  ld = lut_from_selectors(hi_c >> 16, lo >> 16, lo_c >> 16);
 }
 
 // Lookups for a single word (halo words, boundary checks and the debug path).
@@ -173,42 +216,56 @@ __device__ __forceinline__ void lut_interleaved(uint32_t c, uint32_t d, WordLut&
   const uint32_t hi_c = bit_select_not(c >> 4, d, lo_mask);
   const uint32_t lo = bit_select(c, d << 4, lo_mask);
   const uint32_t lo_c = bit_select_not(c, d << 4, lo_mask);
-  A = lut_from_selectors(prmt(c, d, 0xD9C8), hi_c, lo, lo_c);
-  B = lut_from_selectors(prmt(c, d, 0xFBEA), hi_c >> 16, lo >> 16, lo_c >> 16);
+  A = lut_from_selectors(hi_c, lo, lo_c);
+  B = lut_from_selectors(hi_c >> 16, lo >> 16, lo_c >> 16);
 }
 
-// special_cases (Fig. 1) for the four bytes of a word, given the previous
-// word's lookups: prev1 = previous byte.
-__device__ __forceinline__ uint32_t special_cases(const WordLut& prev, const WordLut& cur) {
-  return __funnelshift_l(prev.prev_side, cur.prev_side, 8) & cur.cur_side;
+// The expectation terms of two bytes back and three back, folded per byte:
+// bit 6 of byte k of  2 * flags + 4 * prev1_flags  is
+// (byte >= 0xE0) XOR (its previous byte >= 0xF0).  (Both terms hold only when
+// a lead follows a 4-byte lead directly, an error that the continuation
+// check catches at that lead, so XOR in place of OR never hides an error.)
+// Carries stay below bit 7 of the byte or spill into bits 0..1 of the next
+// byte, outside bit 6.  Integer multiplies: the FMA pipe, not the ALU pipe.
+__device__ __forceinline__ uint32_t back23(uint32_t flags, uint32_t prev1_flags) {
+  return flags * 2u + prev1_flags * 4u;
 }
 
-// must_be_2_3_continuation (Section 6.2) for the four bytes of a word.
-__device__ __forceinline__ uint32_t must_be_2_3(const WordLut& prev, const WordLut& cur) {
-  return (__funnelshift_l(prev.flags, cur.flags, 17) | __funnelshift_l(prev.flags, cur.flags, 26)) &
-         kTwoConts;
+// Error byte of each position of a word, given the word's lookups, its
+// previous bytes' lookups aligned to it (prev1 = x, flags of prev1 = g) and
+// back23 of the bytes two back (h2).  Non-zero iff the position is an error.
+__device__ __forceinline__ uint32_t position_errors(uint32_t x, uint32_t cur_side, uint32_t g,
+                                                    uint32_t h2) {
+  const uint32_t expect = (g | h2) & kContBits;
+  return (x & cur_side) ^ expect;
 }
 
-// Non-zero iff one of the word's four positions is an error (natural order).
+// Error bytes of a natural-order word `cur` after the four bytes whose
+// prev_side, flags and back23 are p, f and h (bytes 1..3 used; h's byte 1 is
+// not needed).
+__device__ __forceinline__ uint32_t word_error_after(uint32_t p, uint32_t f, uint32_t h,
+                                                     const WordLut& cur) {
+  const uint32_t x = __funnelshift_l(p, cur.prev_side, 8);
+  const uint32_t g = __funnelshift_l(f, cur.flags, 8);
+  const uint32_t hc = back23(cur.flags, g);
+  return position_errors(x, cur.cur_side, g, __funnelshift_l(h, hc, 16));
+}
+
+// back23 of a natural-order word on its own: exact in bytes 1..3.
+__device__ __forceinline__ uint32_t back23_word(const WordLut& w) {
+  return back23(w.flags, w.flags << 8);
+}
+
+// Error bytes of the four positions of `cur` (natural order) after `prev`.
 __device__ __forceinline__ uint32_t word_error(const WordLut& prev, const WordLut& cur) {
-  return special_cases(prev, cur) ^ must_be_2_3(prev, cur);
+  return word_error_after(prev.prev_side, prev.flags, back23_word(prev), cur);
 }
 
-// The same for an interleaved word W_m, given W_{m-1} (p1) and W_{m-2} (p2):
-// prev1 = funnel(W_{m-1}, W_m, 16); prev2 = W_{m-1} (flag bit 6 -> bit 7);
-// prev3 = funnel(W_{m-2}, W_{m-1}, 16) (flag bit 5 -> bit 7, so 18 bits).
-__device__ __forceinline__ uint32_t interleaved_error(const WordLut& p2, const WordLut& p1,
-                                                      const WordLut& cur) {
-  const uint32_t sc = __funnelshift_l(p1.prev_side, cur.prev_side, 16) & cur.cur_side;
-  const uint32_t m = ((p1.flags << 1) | __funnelshift_l(p2.flags, p1.flags, 18)) & kTwoConts;
-  return sc ^ m;
-}
-
-// Lookups of an all-ASCII word (also the zero padding before a stream).
+// Lookups of four zero bytes (the ASCII padding before and after a stream).
 __device__ __forceinline__ WordLut ascii_lut() {
   WordLut r;
-  r.prev_side = kAsciiB1H;  // byte_1_high & byte_1_low of an ASCII byte: TOO_LONG only
-  r.cur_side = kAsciiB2H;
+  r.prev_side = kZeroPrevSide;
+  r.cur_side = 0;
   r.flags = 0;
   return r;
 }

@@ -94,33 +94,34 @@ __device__ __forceinline__ uint32_t load_word(const Span& s, uint64_t v) {
   return w & keep_bytes(a, b);
 }
 
-// What lane 0 of a row pair needs from the row pair before it: the lookups of
-// the last two interleaved words (W_6, W_7) of lane 31, i.e. the last four
-// bytes of both rows.  Only their second-stream bytes (1 and 3) are used.
+// What lane 0 of a row pair needs from the row pair before it: the last
+// interleaved word W_7 of lane 31 (the last four bytes of both rows): its
+// prev_side, its flags and its back23 (see lookup.cuh).  Only the
+// second-stream bytes (1 and 3) are used.
 struct Carry {
   uint32_t x7;  // prev_side of W_7
   uint32_t f7;  // flags of W_7
-  uint32_t f6;  // flags of W_6
+  uint32_t h7;  // back23 of W_7
 };
 
 __device__ __forceinline__ Carry ascii_carry() {
   const WordLut a = ascii_lut();
-  return Carry{a.prev_side, a.flags, a.flags};
+  return Carry{a.prev_side, a.flags, 0u};
 }
 
 // Carry for a stream whose previous four bytes (natural order) are `halo`.
 __device__ __forceinline__ Carry halo_carry(uint32_t halo) {
   const WordLut h = lut_word(halo);
-  return Carry{prmt(h.prev_side, 0, 0x3020), prmt(h.flags, 0, 0x3020), prmt(h.flags, 0, 0x1000)};
+  return Carry{prmt(h.prev_side, 0, 0x3020), prmt(h.flags, 0, 0x3020),
+               prmt(back23_word(h), 0, 0x3020)};
 }
 
-// The carry's last four bytes as natural-order lookups (for a word check).
-__device__ __forceinline__ WordLut carry_as_word(const Carry& c) {
-  WordLut w;
-  w.prev_side = c.x7;  // byte 3 = the byte just before
-  w.cur_side = 0;
-  w.flags = prmt(c.f6, c.f7, 0x7531);
-  return w;
+// Error bytes of the first four positions of a tile's row 0 (natural order,
+// word w) after the carry: the check an all-ASCII tile still makes.
+__device__ __forceinline__ uint32_t word_error_after_carry(const Carry& c, uint32_t w) {
+  // the carry's stream-1 bytes 1 and 3 are the last two bytes before the tile
+  return word_error_after(prmt(c.x7, 0, 0x3144), prmt(c.f7, 0, 0x3144), prmt(c.h7, 0, 0x3144),
+                          lut_word(w));
 }
 
 template <int ROWS>
@@ -192,7 +193,7 @@ __device__ __forceinline__ void check_tile(const uint4 (&d)[ROWS], Carry& carry,
 #pragma unroll
       for (int m = 0; m < 8; ++m) e[p][m] = 0;
     if (lane == 0) {
-      const uint32_t first = word_error(carry_as_word(carry), lut_word(d[0].x));
+      const uint32_t first = word_error_after_carry(carry, d[0].x);
       e[0][0] = prmt(first, 0, 0x4140);  // positions 0, 1 of row 0
       e[0][1] = prmt(first, 0, 0x4342);  // positions 2, 3 of row 0
     }
@@ -207,22 +208,29 @@ __device__ __forceinline__ void check_tile(const uint4 (&d)[ROWS], Carry& carry,
     lut_interleaved(c.y, n.y, W[2], W[3]);
     lut_interleaved(c.z, n.z, W[4], W[5]);
     lut_interleaved(c.w, n.w, W[6], W[7]);
-    // left neighbour's W_7, W_6; lane 0 takes its first stream from the carry
+    // flags of each word's previous bytes (prev1) and back23 of each word
+    uint32_t g[8], h[8];
+#pragma unroll
+    for (int m = 1; m < 8; ++m) {
+      g[m] = __funnelshift_l(W[m - 1].flags, W[m].flags, 16);
+      h[m] = back23(W[m].flags, g[m]);
+    }
+    // left neighbour's W_7; lane 0 takes its first stream from the carry
     // (the row before) and its second stream from lane 31 of the first row
     const uint32_t x7 = __shfl_sync(kFull, W[7].prev_side, left);
     const uint32_t f7 = __shfl_sync(kFull, W[7].flags, left);
-    const uint32_t f6 = __shfl_sync(kFull, W[6].flags, left);
-    WordLut L7, L6;
-    L7.prev_side = prmt(carry.x7, x7, merge_sel);
-    L7.flags = prmt(carry.f7, f7, merge_sel);
-    L7.cur_side = 0;
-    L6.flags = prmt(carry.f6, f6, merge_sel);
-    L6.prev_side = L6.cur_side = 0;
-    carry = Carry{x7, f7, f6};
-    e[p][0] = interleaved_error(L6, L7, W[0]);
-    e[p][1] = interleaved_error(L7, W[0], W[1]);
+    const uint32_t h7 = __shfl_sync(kFull, h[7], left);
+    const uint32_t lx = prmt(carry.x7, x7, merge_sel);
+    const uint32_t lf = prmt(carry.f7, f7, merge_sel);
+    const uint32_t lh = prmt(carry.h7, h7, merge_sel);
+    carry = Carry{x7, f7, h7};
+    g[0] = __funnelshift_l(lf, W[0].flags, 16);
+    h[0] = back23(W[0].flags, g[0]);
+    e[p][0] = position_errors(__funnelshift_l(lx, W[0].prev_side, 16), W[0].cur_side, g[0], lh);
 #pragma unroll
-    for (int m = 2; m < 8; ++m) e[p][m] = interleaved_error(W[m - 2], W[m - 1], W[m]);
+    for (int m = 1; m < 8; ++m)
+      e[p][m] = position_errors(__funnelshift_l(W[m - 1].prev_side, W[m].prev_side, 16),
+                                W[m].cur_side, g[m], h[m - 1]);
   }
 }
 

@@ -35,20 +35,25 @@ __global__ void __launch_bounds__(kBlockThreads) validate_kernel(Span s, uint64_
   if (__any_sync(kFull, err != 0) && (threadIdx.x & (kLanes - 1)) == 0) clear_result(out_valid);
 }
 
-// One thread per 4-byte word of the virtual layout.
-__global__ void classify_debug_kernel(Span s, uint8_t* out_special, uint8_t* out_must23) {
+// One thread per 4-byte word of the virtual layout: the parts of each
+// position's classification byte (see lookup.cuh), from the same lookups and
+// the same error function as the validators.
+__global__ void classify_debug_kernel(Span s, uint8_t* out_special, uint8_t* out_cont) {
   const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t words = s.granules * 4;
   if (k >= words) return;
   const WordLut prev = k == 0 ? ascii_lut() : lut_word(load_word(s, 4 * k - 4));
   const WordLut cur = lut_word(load_word(s, 4 * k));
-  const uint32_t sc = special_cases(prev, cur);
-  const uint32_t m = must_be_2_3(prev, cur);
+  const uint32_t err = word_error(prev, cur);
+  const uint32_t matched = __funnelshift_l(prev.prev_side, cur.prev_side, 8) & cur.cur_side;
   for (int j = 0; j < 4; ++j) {
     const uint64_t v = 4 * k + j;  // virtual position; output index v - off
     if (v < s.off || v >= s.off + s.n + 3) continue;
-    out_special[v - s.off] = (uint8_t)(sc >> (8 * j));
-    out_must23[v - s.off] = (uint8_t)(m >> (8 * j));
+    const uint32_t is_cont = (cur.cur_side >> (8 * j + 6)) & 1u;
+    // bit 6 of the error byte is is_cont XOR expected
+    const uint32_t expected = ((err >> (8 * j + 6)) & 1u) ^ is_cont;
+    out_special[v - s.off] = (uint8_t)((matched >> (8 * j)) & kSpecialBits);
+    out_cont[v - s.off] = (uint8_t)(expected | (is_cont << 1));
   }
 }
 
@@ -127,12 +132,12 @@ cudaError_t launch_validate(const uint8_t* data, uint64_t n, uint8_t* out_valid,
 }
 
 cudaError_t launch_classify_debug(const uint8_t* data, uint64_t n, uint8_t* out_special,
-                                  uint8_t* out_must23, cudaStream_t st) {
+                                  uint8_t* out_cont, cudaStream_t st) {
   const Span s = make_span(data, n);
   const uint64_t words = s.granules * 4;
   const unsigned block = 256;
   const uint64_t grid = (words + block - 1) / block;
-  classify_debug_kernel<<<(unsigned)grid, block, 0, st>>>(s, out_special, out_must23);
+  classify_debug_kernel<<<(unsigned)grid, block, 0, st>>>(s, out_special, out_cont);
   return cudaGetLastError();
 }
 

@@ -6,9 +6,10 @@
 //
 // Every thread runs kChains independent dependency chains of one operation,
 // so that issue, not latency, limits the rate; a full grid (2048 threads per
-// SM) runs `iters` rounds.  Each block reads the SM cycle counter before and
-// after its loop; all blocks of an SM run at once, so ops per clock per SM =
-// (ops of the blocks on an SM) / (the blocks' median cycle span).
+// SM) runs `iters` rounds.  The launch is timed with CUDA events: operations
+// per second, divided by SMs and the SM clock the caller sampled, give
+// operations per clock per SM.  (Each block also records the span of its
+// loop in clock64() ticks.)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -68,9 +69,10 @@ cudaError_t run(unsigned blocks, uint32_t iters, long long* cycles, uint32_t* si
 
 // op: 0 LOP3, 1 PRMT, 2 SHF, 3 IMAD, 4 PRMT+IMAD mixed.  cycles_out: host
 // int64[blocks_per_sm * sm_count]; *ops_per_block receives the operations one
-// block executes.  Returns 0 on success, else the CUDA error code.
+// block executes, *ms_out the launch's event time.  Returns 0 on success,
+// else the CUDA error code.
 extern "C" int alu_probe_run(int op, int blocks_per_sm, unsigned iters, long long* cycles_out,
-                             double* ops_per_block, int* sm_count_out) {
+                             double* ops_per_block, int* sm_count_out, float* ms_out) {
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -78,8 +80,12 @@ extern "C" int alu_probe_run(int op, int blocks_per_sm, unsigned iters, long lon
   const unsigned blocks = (unsigned)(sms * blocks_per_sm);
   long long* cyc = nullptr;
   uint32_t* sink = nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
   e = cudaMalloc(&cyc, sizeof(long long) * blocks);
   if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  if (e == cudaSuccess) e = cudaEventRecord(t0);
   if (e == cudaSuccess) {
     switch (op) {
       case 0: e = run<0>(blocks, iters, cyc, sink); break;
@@ -89,9 +95,13 @@ extern "C" int alu_probe_run(int op, int blocks_per_sm, unsigned iters, long lon
       default: e = run<4>(blocks, iters, cyc, sink); break;
     }
   }
+  if (e == cudaSuccess) e = cudaEventRecord(t1);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms_out, t0, t1);
   if (e == cudaSuccess)
     e = cudaMemcpy(cycles_out, cyc, sizeof(long long) * blocks, cudaMemcpyDeviceToHost);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
   cudaFree(cyc);
   cudaFree(sink);
   *ops_per_block = (double)kThreads * kChains * (double)iters;

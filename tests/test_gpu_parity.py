@@ -60,27 +60,73 @@ def de_bruijn_256_2() -> np.ndarray:
 # --------------------------------------------------------------------------
 # classification intermediates
 # --------------------------------------------------------------------------
+# The kernels' special-row bits, in the order of the paper's Table 8 bits.
+PAPER_BIT_OF = ((0x01, 0x20), (0x02, 0x04), (0x04, 0x10), (0x08, 0x08), (0x10, 0x40))
+
+
+def to_paper_bits(sc: np.ndarray) -> np.ndarray:
+    out = np.zeros_like(sc)
+    for ours, paper in PAPER_BIT_OF:
+        out |= np.where(sc & ours, paper, 0).astype(sc.dtype)
+    return out
+
+
+def check_against_paper(buf: np.ndarray, sc: np.ndarray, cont: np.ndarray):
+    """Per position of buf + 3 zeros (zeros before): the special-row bits
+    equal the paper's (Table 7 through lookup_aid) except where an ASCII byte
+    precedes a continuation (an error either way); cont bit 1 is
+    'continuation', cont bit 0 is 'previous byte >= 0xC0, or exactly one of
+    the two terms of must_be_2_3' (both terms hold only where a lead follows a
+    4-byte lead, an error that position i-2 shows)."""
+    zeros = np.zeros(3, np.uint8)
+    padded = np.concatenate([buf, zeros])
+    paper = lookup_aid.classify(padded, zeros)["special_cases"]
+    must23 = lookup_aid.must_be_2_3_continuation(padded, zeros)
+    prev1 = np.concatenate([zeros[:1], padded[:-1]])
+    is_cont = (padded & 0xC0) == 0x80
+    free = (prev1 < 0x80) & is_cont
+    want_sc = to_paper_bits(sc)
+    assert np.array_equal(np.where(free, 0, want_sc), np.where(free, 0, paper & 0x7C))
+    assert np.array_equal((cont >> 1) & 1, is_cont.astype(np.uint8))
+    prev2 = np.concatenate([zeros[:2], padded[:-2]])
+    prev3 = np.concatenate([zeros, padded[:-3]])
+    term2, term3 = prev2 >= 0xE0, prev3 >= 0xF0
+    assert np.array_equal(must23 != 0, term2 | term3)  # the paper's must_be_2_3
+    want = (prev1 >= 0xC0) | (term2 ^ term3)
+    assert np.array_equal(cont & 1, want.astype(np.uint8))
+    # where both terms hold, position i-2 is an error: a lead right after a
+    # 4-byte lead, where a continuation is expected
+    both = np.flatnonzero(term2 & term3)
+    assert np.all((cont[both - 2] & 1) == 1) and np.all(((cont[both - 2] >> 1) & 1) == 0)
+    assert not np.any(cont & 0xFC) and not np.any(sc & 0xE0)
+
+
 def test_table8_special_cases(golden_dir):
     rows = dict(read_hex_rows(os.path.join(golden_dir, "table8.txt")))
     buf = np.frombuffer(rows["input"], dtype=np.uint8)
-    sc, m = u.utf8_classify_debug(dev(buf))
-    sc = sc.cpu().numpy()
-    assert bytes(sc[:len(buf)]) == rows["special_cases"]
+    sc, cont = u.utf8_classify_debug(dev(buf))
+    sc, cont = sc.cpu().numpy()[:len(buf)], cont.cpu().numpy()[:len(buf)]
+    paper = np.frombuffer(rows["special_cases"], np.uint8)
+    # Table 8's text is valid: no special row matches, and bit 7 of the
+    # paper's special_cases (two continuations in a row) marks exactly the
+    # positions that are continuations and expect one without a lead just
+    # before (must_be_2_3)
+    assert not np.any(sc) and not np.any(paper & 0x7F)
+    assert np.array_equal(cont & 1, (cont >> 1) & 1)
+    prev1 = np.concatenate([[0], buf[:-1]]).astype(np.uint8)
+    assert np.array_equal((paper >> 7) & 1, ((cont >> 1) & 1) & (prev1 < 0xC0))
 
 
 def test_classification_every_byte_pair():
     seq = de_bruijn_256_2()
     pairs = set(zip(seq[:-1].tolist(), seq[1:].tolist()))
     assert len(pairs) == 65536
-    sc, m = u.utf8_classify_debug(dev(seq))
-    sc, m = sc.cpu().numpy(), m.cpu().numpy()
-    padded = np.concatenate([seq, np.zeros(3, np.uint8)])
-    want = lookup_aid.classify(padded, np.zeros(3, np.uint8))["special_cases"]
-    want_m = lookup_aid.must_be_2_3_continuation(padded, np.zeros(3, np.uint8))
-    assert np.array_equal(sc, want)
-    assert np.array_equal(m, want_m)
-    table = lookup_aid.pair_special_cases()
-    assert np.array_equal(sc[1:len(seq)], table[seq[:-1], seq[1:]])
+    sc, cont = u.utf8_classify_debug(dev(seq))
+    sc, cont = sc.cpu().numpy(), cont.cpu().numpy()
+    check_against_paper(seq, sc, cont)
+    pair = lookup_aid.pair_special_cases()[seq[:-1], seq[1:]] & 0x7C
+    free = (seq[:-1] < 0x80) & ((seq[1:] & 0xC0) == 0x80)
+    assert np.array_equal(np.where(free, 0, to_paper_bits(sc[1:len(seq)])), np.where(free, 0, pair))
 
 
 @pytest.mark.parametrize("shift", [0, 1, 5, 15])
@@ -89,12 +135,8 @@ def test_classification_random_misaligned(shift):
     buf = CLASS_BYTES[rng.integers(0, CLASS_BYTES.size, 100_000)]
     t = torch.zeros(buf.size + 16, dtype=torch.uint8, device="cuda")
     t[shift:shift + buf.size] = dev(buf)
-    sc, m = u.utf8_classify_debug(t[shift:shift + buf.size])
-    padded = np.concatenate([buf, np.zeros(3, np.uint8)])
-    assert np.array_equal(sc.cpu().numpy(),
-                          lookup_aid.classify(padded, np.zeros(3, np.uint8))["special_cases"])
-    assert np.array_equal(m.cpu().numpy(),
-                          lookup_aid.must_be_2_3_continuation(padded, np.zeros(3, np.uint8)))
+    sc, cont = u.utf8_classify_debug(t[shift:shift + buf.size])
+    check_against_paper(buf, sc.cpu().numpy(), cont.cpu().numpy())
 
 
 # --------------------------------------------------------------------------
