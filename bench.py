@@ -62,7 +62,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--buffer-bytes", type=int, default=GIB)
     ap.add_argument("--no-extras", action="store_true", help="skip batch/serving extras")
-    ap.add_argument("--legs", default="main,e2e,cpu,alu,cfg1mib,locate,batch,serve,stream,copy,small",
+    ap.add_argument("--legs", default="main,e2e,cpu,alu,cfg1mib,locate,fsm,batch,serve,stream,copy,small",
                     help="comma-separated legs to run (profiling runs pick one)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-memory leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
@@ -557,6 +557,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         line["cpu_baseline"] = oracle_baseline(host, names, args.cpu_seconds)
     if world == 1 and "locate" in legs:
         line["locate"] = bench_locate(u, torch, dev, names, stream, flags)
+    if world == 1 and "fsm" in legs:
+        line["fsm"] = bench_fsm(u, torch, dev, names, stream, flags, peak)
     if world == 1 and "cfg1mib" in legs:
         line["config_1mib"] = bench_config_1mib(u, torch)
     if world == 1 and legs & {"batch", "serve", "stream", "copy", "small"}:
@@ -612,6 +614,42 @@ def bench_locate(u, torch, dev, names, stream, flags=None, steps: int = 30) -> d
             "bytes_per_step": int(sum(sizes)), "kernels_per_buffer": 2,
             "rules": dict(zip(names, rule)), "results_consistent": ok,
             "early_reject": bench_early_reject(u, torch, dev, names, stream)}
+
+
+def bench_fsm(u, torch, dev, names, stream, flags, peak: float, steps: int = 20) -> dict:
+    """The paper's finite-state validator (Section 5) on the GPU over the main
+    leg's ten buffers (one memset and one fsm_kernel launch per buffer), next
+    to the `lookup` kernel: validated GB/s, fraction of the measured HBM peak
+    and its flags against the main leg's."""
+    res = torch.empty(len(dev), dtype=torch.uint8, device="cuda")
+
+    def one_step():
+        for i, t in enumerate(dev):
+            u.utf8_validate_fsm_async(t, res[i:i + 1], stream=stream)
+
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    per = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in dev] for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            one_step()
+        a.record(stream)
+        for k in range(steps):
+            for i, t in enumerate(dev):
+                per[k][i][0].record(stream)
+                u.utf8_validate_fsm_async(t, res[i:i + 1], stream=stream)
+                per[k][i][1].record(stream)
+        b.record(stream)
+    stream.synchronize()
+    total = sum(t.numel() for t in dev) * steps
+    gbs = total / (a.elapsed_time(b) / 1e3) / 1e9
+    ms = np.array([[x.elapsed_time(y) for x, y in row] for row in per])
+    return {"gbs": round(gbs, 1), "pct_of_hbm_peak": round(100 * gbs / peak, 1), "steps": steps,
+            "per_variant_gbs": {nm: round(dev[i].numel() / (ms[:, i].mean() / 1e3) / 1e9, 1)
+                                for i, nm in enumerate(names)},
+            "flags_match_lookup": res.cpu().numpy().tolist() == list(flags),
+            "kernel": "fsm_kernel: 9 x 256 transition table in shared memory, 4 machines per "
+                      "lane over 512-byte regions"}
 
 
 def bench_early_reject(u, torch, dev, names, stream, reps: int = 7) -> dict:

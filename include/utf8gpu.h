@@ -73,6 +73,17 @@ int utf8_validate_async(const uint8_t* data, size_t len, uint8_t* out_valid,
                         cudaStream_t stream);
 
 /*
+ * The paper's finite-state validator (Section 5: nine states, the continuation
+ * ranges 80..8F / 90..9F / A0..BF, one transition per byte) on the GPU, for
+ * comparison with the `lookup` path of utf8_validate_async; same arguments,
+ * result and status.  Each lane runs four machines over regions of 512 bytes
+ * that start at character boundaries (the paper's interleaved regions); the
+ * table lives in shared memory.  Asynchronous, no allocation.
+ */
+int utf8_validate_fsm_async(const uint8_t* data, size_t len, uint8_t* out_valid,
+                            cudaStream_t stream);
+
+/*
  * Validates `count` strings in one launch sequence.  String i is
  * data[offsets[i] .. offsets[i+1]) (int64 device array of count + 1
  * non-decreasing entries, offsets[0] >= 0); each string is checked on its own

@@ -22,6 +22,7 @@ from ._lib import (  # noqa: F401
     utf8_tune_cache_save,
     utf8_validate,
     utf8_validate_async,
+    utf8_validate_fsm_async,
     utf8_validate_batch,
     utf8_validate_host,
     utf8_validate_host_noalloc,

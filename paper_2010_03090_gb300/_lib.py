@@ -20,6 +20,7 @@ EXPORTS = (
     "utf8_stream_update", "utf8_stream_finish", "utf8_stream_destroy", "utf8_copy_validate",
     "utf8_locate_error", "utf8_locate_error_async", "utf8_locate_errors_batch",
     "utf8_check_offsets", "utf8_validate_batch_desc", "utf8_set_early_exit",
+    "utf8_validate_fsm_async",
 )
 
 # Section 3's rules a-f as the library numbers them (enum utf8_rule).
@@ -56,6 +57,8 @@ def lib() -> ctypes.CDLL:
             L.utf8_validate.restype = ctypes.c_bool
             L.utf8_validate_async.argtypes = [vp, sz, vp, vp]
             L.utf8_validate_async.restype = i32
+            L.utf8_validate_fsm_async.argtypes = [vp, sz, vp, vp]
+            L.utf8_validate_fsm_async.restype = i32
             L.utf8_validate_batch.argtypes = [vp, vp, i64, vp, vp]
             L.utf8_validate_batch.restype = i32
             L.utf8_validate_host.argtypes = [vp, sz, vp]
@@ -160,6 +163,19 @@ def utf8_validate_async(data, out_valid=None, stream=None):
         out_valid = torch.empty(1, dtype=torch.uint8, device=data.device)
     q, _ = _dev(out_valid, "uint8", "out_valid")
     _check(lib().utf8_validate_async(p or None, n, q, _stream(stream)), "utf8_validate_async")
+    return out_valid
+
+
+def utf8_validate_fsm_async(data, out_valid=None, stream=None):
+    """The paper's finite-state validator (Section 5) on the GPU, for
+    comparison: queues it; returns a 1-element uint8 CUDA tensor (1 = valid)."""
+    import torch
+    p, n = _dev(data, "uint8", "data")
+    if out_valid is None:
+        out_valid = torch.empty(1, dtype=torch.uint8, device=data.device)
+    q, _ = _dev(out_valid, "uint8", "out_valid")
+    _check(lib().utf8_validate_fsm_async(p or None, n, q, _stream(stream)),
+           "utf8_validate_fsm_async")
     return out_valid
 
 

@@ -205,6 +205,19 @@ int utf8_validate_async(const uint8_t* data, size_t len, uint8_t* out_valid,
   return cuda_status(launch_validate(data, len, out_valid, config_of(*d), d->sm_count, stream));
 }
 
+int utf8_validate_fsm_async(const uint8_t* data, size_t len, uint8_t* out_valid,
+                            cudaStream_t stream) {
+  if (out_valid == nullptr || (data == nullptr && len > 0))
+    return set_status(UTF8_ERR_INVALID_ARG);
+  DeviceState* d = device();
+  if (!d) return UTF8_ERR_CUDA;
+  if (!is_device_memory(out_valid) || (len > 0 && !is_device_memory(data)))
+    return set_status(UTF8_ERR_INVALID_ARG);
+  cudaError_t e = cudaMemsetAsync(out_valid, 1, 1, stream);
+  if (e == cudaSuccess && len > 0) e = launch_validate_fsm(data, len, out_valid, d->sm_count, stream);
+  return cuda_status(e);
+}
+
 int utf8_validate_batch(const uint8_t* data, const int64_t* offsets, int64_t count,
                         uint8_t* out_valid, cudaStream_t stream) {
   if (count < 0) return set_status(UTF8_ERR_INVALID_ARG);

@@ -138,12 +138,23 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
   // strings that can hold a position of this warp: b0 - 1 .. b1 - 1
   const int64_t own_hi = b1 < count ? b1 : count;
 
-  __shared__ uint32_t err_smem[kBlockThreads / kLanes][ROWS / 2 * 8 * kLanes];
-  uint32_t* err_words = err_smem[threadIdx.x / kLanes];
+  // Per warp: the 8 bytes before the current tile (bytes 8..15), then the
+  // tile itself (from byte 16), staged so that boundary windows are taken
+  // from it instead of being read again from memory.  A tile with errors
+  // reuses the tile part for its error words once its windows are taken.
+  __shared__ __align__(16) uint32_t stage_smem[kBlockThreads / kLanes][4 + ROWS * kLanes * 4];
+  uint32_t* stage = stage_smem[threadIdx.x / kLanes];
+  uint32_t* err_words = stage + 4;
+  static_assert(ROWS / 2 * 8 * kLanes == ROWS * kLanes * 4, "error words fit the tile part");
 
   const uint32_t merge_sel = carry_merge_selector(lane);
   Carry carry = ascii_carry();
-  if (t0 > 0) carry = halo_carry(load_word(region, t0 * kTileBytes - 4));
+  const uint32_t halo = t0 > 0 ? load_word(region, t0 * kTileBytes - 4) : 0u;
+  if (t0 > 0) carry = halo_carry(halo);
+  if (lane == 0) {
+    stage[2] = t0 > 0 ? load_word(region, t0 * kTileBytes - 8) : 0u;
+    stage[3] = halo;
+  }
   // Tiles are counted from t0 in 32 bits (a warp's run is far below 2^32
   // tiles); [r_in0, r_in1) are its tiles wholly inside the region.
   const uint32_t n_tiles = (uint32_t)(t1 - t0);
@@ -163,6 +174,11 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
   int64_t next_group = b0;
   int64_t group_last = -1;
   int64_t g_off = INT64_MAX;
+  // The window [o_j - 4, o_j + 4) of this lane's boundary, taken from the
+  // staged tile holding its last byte; `win_global` when that tile's staged
+  // bytes were already replaced (then it is read from memory at the check).
+  uint32_t win_lo = 0, win_hi = 0;
+  bool win_global = false;
   int64_t prev_off = b0 > 0 ? offsets[b0 - 1] : INT64_MIN;
   uint32_t due = 0xFFFFFFFFu;
   auto group_offsets = [&](int64_t first) -> int64_t {
@@ -175,7 +191,9 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
       group_last = (next_group + kLanes < b1 ? next_group + kLanes : b1) - 1;
       g_off = g_nxt;
       const int64_t last_off = __shfl_sync(kFull, g_off, (int)(group_last - next_group));
-      due = (uint32_t)(((uint64_t)(last_off - vbase) / kTileBytes) - t0);
+      // checked on the tile holding the last byte of its last window
+      due = (uint32_t)(((uint64_t)(last_off + 3 - vbase) / kTileBytes) - t0);
+      win_global = false;
       g_nxt = group_last + 1 < b1 ? group_offsets(group_last + 1) : INT64_MAX;
     } else {
       g_off = INT64_MAX;
@@ -183,6 +201,22 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
     }
   };
   open_group();
+
+  // Takes the windows that end in the staged tile starting at tile_lo.
+  auto take_windows = [&](int64_t tile_lo, bool staged) {
+    const int64_t end = g_off + 3 - tile_lo;  // last window byte, tile-relative
+    if (g_off != INT64_MAX && end >= 0 && end < (int64_t)kTileBytes) {
+      if (!staged) {
+        win_global = true;
+      } else {
+        const uint32_t sb = (uint32_t)(end - 7 + 16);  // window start in stage bytes: 9 ..
+        const uint32_t w = sb >> 2, sh = 8u * (sb & 3u);
+        const uint32_t u0 = stage[w], u1 = stage[w + 1], u2 = (sb & 3u) ? stage[w + 2] : 0u;
+        win_lo = __funnelshift_r(u0, u1, sh);
+        win_hi = __funnelshift_r(u1, u2, sh);
+      }
+    }
+  };
 
   uint4 next[ROWS];  // the next tile's loads, issued one tile ahead
   if (r_in0 == 0 && r_in1 > 0) load_tile_interior<ROWS>(lane_ptr, next);
@@ -197,6 +231,12 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
       if (i + 1 >= r_in0 && i + 1 < r_in1) load_tile_interior<ROWS>(lane_ptr + kTileBytes, next);
       else load_tile_checked<ROWS>(region, t0 + i + 1, lane, next);
     }
+    const int64_t tile_lo = vbase + (int64_t)((t0 + i) * kTileBytes);
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) reinterpret_cast<uint4*>(stage + 4)[r * kLanes + lane] = d[r];
+    __syncwarp();
+    take_windows(tile_lo, true);
+    bool staged = true;  // the stage still holds this tile
     uint32_t e[ROWS / 2][8];
     check_tile<ROWS>(d, carry, lane, merge_sel, e);
     uint32_t any_err = 0;
@@ -213,7 +253,8 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
     // one at a time: they go through shared memory so that each lane walks
     // its own in one rolled loop.
     if (__any_sync(kFull, any_err != 0)) {
-      const int64_t tile_lo = vbase + (int64_t)((t0 + i) * kTileBytes);
+      staged = false;
+      __syncwarp();  // every lane has taken its windows from the stage
       static_assert(ROWS / 2 * 8 <= 32, "one bit per error word");
       uint32_t nonzero = 0;  // bit w: error word w of this lane is non-zero
 #pragma unroll
@@ -237,7 +278,10 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
         int64_t p = INT64_MAX;
         if (bits != 0) {
           const int byte = (__ffs(bits) - 1) >> 3;
-          bits &= ~(0xFFu << (8 * byte));
+          // bytes `byte` and byte + 2 are positions 2m and 2m+1 of one row:
+          // the first decides for both (the same string, or 2m+1 starts one,
+          // and a string's first three bytes are the head check's)
+          bits &= ~(0x00FF00FFu << (8 * byte));
           p = tile_lo + (int64_t)interleaved_position<ROWS>(k >> 3, k & 7, byte, lane);
         }
         uint32_t pending = __ballot_sync(kFull, p != INT64_MAX);
@@ -285,7 +329,15 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
         const int64_t lo = j >= 1 ? o_prev : oj;
         const int64_t hi = j < count ? o_next : oj;
         uint32_t w_tail, w_head;  // bytes [o_j - 4, o_j) and [o_j, o_j + 4), in [lo, hi)
-        gather8(data, oj - 4, lo, hi, w_tail, w_head);
+        if (win_global || oj + 3 >= tile_lo + (int64_t)kTileBytes) {
+          // window replaced in the stage, or ending past this warp's last tile
+          gather8(data, oj - 4, lo, hi, w_tail, w_head);
+        } else {
+          const int64_t x = oj - 4;
+          const int ka = (int)((lo > x ? lo : x) - x), kb = (int)((hi < x + 8 ? hi : x + 8) - x);
+          w_tail = win_lo & keep_bytes(ka, kb);
+          w_head = win_hi & keep_bytes(ka - 4, kb - 4);
+        }
         WordLut tail, head;
         lut_pair(w_tail, w_head, tail, head);
         if (j >= 1) {  // positions o_j .. o_j+3 after string j-1 (virtual zeros)
@@ -300,7 +352,15 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
       prev_off = __shfl_sync(kFull, g_off, (int)(group_last - next_group));
       next_group = group_last + 1;
       open_group();
+      take_windows(tile_lo, staged);
     }
+    // the 8 bytes before the next tile: this tile's last 8 (lane 31, last row)
+    __syncwarp();
+    if (lane == kLanes - 1) {
+      stage[2] = d[ROWS - 1].z;
+      stage[3] = d[ROWS - 1].w;
+    }
+    __syncwarp();
   }
 }
 

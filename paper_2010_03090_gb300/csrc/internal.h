@@ -39,6 +39,11 @@ cudaError_t preload_validate_kernels();
 bool early_exit_enabled();
 int set_early_exit(int enable);  // returns the previous setting (0 or 1)
 
+// The paper's finite-state validator (Section 5) over one buffer (fsm.cu);
+// the result byte must hold 1 before the launch.
+cudaError_t launch_validate_fsm(const uint8_t* data, uint64_t n, uint8_t* out_valid, int sm_count,
+                                cudaStream_t st);
+
 cudaError_t launch_classify_debug(const uint8_t* data, uint64_t n, uint8_t* out_special,
                                   uint8_t* out_cont, cudaStream_t st);
 
