@@ -49,7 +49,7 @@
 // outside 0x5F.  This decides exactly the paper's boolean: an exhaustive test
 // checks the tables against Table 7's rows (the special bits equal the
 // paper's wherever the previous byte is not ASCII) and the whole check
-// against the oracle on every class string of up to seven bytes.
+// against the oracle on every class string of up to six bytes.
 #pragma once
 #include <stdint.h>
 
