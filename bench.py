@@ -745,12 +745,33 @@ def bench_batch(u, torch, stream, peak: float, sample: int = 20000,
         stream.synchronize()
         per_ms = (time.perf_counter() - t) * 1e3
     per_gbs = int(offsets[sample] - offsets[0]) / (per_ms / 1e3) / 1e9
+    # the descriptor form: one captured graph (flag set + batch pass) replayed
+    desc = torch.tensor(u.batch_desc_values(d, o, out), dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(stream):
+        u.utf8_validate_batch_desc(desc, stream=stream)
+    stream.synchronize()
+    dgraph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(dgraph, stream=stream):
+        u.utf8_validate_batch_desc(desc, stream=stream)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            dgraph.replay()
+        a.record(stream)
+        for _ in range(reps):
+            dgraph.replay()
+        b.record(stream)
+    stream.synchronize()
+    desc_ms = a.elapsed_time(b) / reps
+    desc_ok = bool(torch.equal(out, u.utf8_validate_batch(d, o)))
     res = {"strings": int(offsets.size - 1), "bytes": int(data.size), "launch": "one CUDA graph",
            "ms": round(ms, 4), "gbs": round(batch_gbs, 1),
            "pct_of_hbm_peak": round(100 * moved / (ms / 1e3) / 1e9 / peak, 1),
            "per_string_launch_gbs": round(per_gbs, 3),
            "per_string_launch_sample": sample,
-           "speedup_vs_per_string": round(batch_gbs / per_gbs, 1)}
+           "speedup_vs_per_string": round(batch_gbs / per_gbs, 1),
+           "descriptor_graph": {"ms": round(desc_ms, 4),
+                                "gbs": round(data.size / (desc_ms / 1e3) / 1e9, 1),
+                                "flags_match": desc_ok}}
     if locate:
         info = torch.empty((offsets.size - 1, 2), dtype=torch.int64, device="cuda")
         with torch.cuda.stream(stream):

@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kBlockThreads)
 // The same pass with its arguments read from a device descriptor when it
 // runs, so that one captured graph serves any batch written into it.
 template <int ROWS>
-__global__ void __launch_bounds__(kBlockThreads) batch_desc_kernel(const utf8_batch_desc* desc) {
+__global__ void __launch_bounds__(kBlockThreads, 2) batch_desc_kernel(const utf8_batch_desc* desc) {
   const utf8_batch_desc d = *desc;
   if (d.count <= 0) return;
   batch_body<ROWS, false>(d.data, d.offsets, d.count, d.out_valid, nullptr);

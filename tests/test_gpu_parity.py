@@ -454,6 +454,37 @@ def test_tiny_batches_around_group_sizes():
                 assert np.array_equal(rule.cpu().numpy(), want_rule), (count, trial, shift)
 
 
+def test_batch_dense_errors_short_strings():
+    """Many short strings with most tiles holding an error: boundary groups
+    then open on tiles whose staged bytes already hold error words, and many
+    windows end past a warp's last tile (one tile per warp), so the kernel's
+    fallback reads run; errors sit in the first and last three bytes of
+    strings too.  Flags and error locations against the oracle."""
+    rng = np.random.default_rng(29)
+    for shift in (0, 3, 9):
+        lens = rng.integers(0, 48, 60_000)
+        strings = []
+        for i, n in enumerate(lens):
+            s = synth.fill(int(n), synth.UNIFORM, seed=shift * 100_000 + i)
+            if n and rng.random() < 0.3:
+                k = rng.integers(0, 4)
+                at = int(rng.integers(0, min(3, n))) if k == 0 else \
+                    int(n - 1 - rng.integers(0, min(3, n))) if k == 1 else int(rng.integers(0, n))
+                s[at] = CLASS_BYTES[rng.integers(0, CLASS_BYTES.size)]
+            strings.append(s)
+        offsets = synth.offsets_of([x.size for x in strings])
+        data = np.concatenate(strings)
+        shifted = np.concatenate([np.full(shift, 0x41, np.uint8), data])
+        want = oracle.valid_batch(data, offsets)
+        assert (want == 0).mean() > 0.1
+        assert np.array_equal(batch_flags(shifted, offsets + shift), want), shift
+        pos, rule = u.error_info_fields(u.utf8_locate_errors_batch(
+            dev(shifted), torch.from_numpy(offsets + shift).cuda()))
+        want_pos, want_rule = oracle.locate_batch(data, offsets)
+        assert np.array_equal(pos.cpu().numpy(), want_pos), shift
+        assert np.array_equal(rule.cpu().numpy(), want_rule), shift
+
+
 def test_check_offsets():
     ok = [[0, 3, 3, 10], [5], [0, 0, 0]]
     bad = [[0, 5, 3, 10], [-1, 2, 3], [0, 1, 2, 1]]
