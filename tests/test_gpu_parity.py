@@ -463,17 +463,18 @@ def test_batch_dense_errors_short_strings():
     rng = np.random.default_rng(29)
     for shift in (0, 3, 9):
         lens = rng.integers(0, 48, 60_000)
-        strings = []
-        for i, n in enumerate(lens):
-            s = synth.fill(int(n), synth.UNIFORM, seed=shift * 100_000 + i)
-            if n and rng.random() < 0.3:
-                k = rng.integers(0, 4)
-                at = int(rng.integers(0, min(3, n))) if k == 0 else \
-                    int(n - 1 - rng.integers(0, min(3, n))) if k == 1 else int(rng.integers(0, n))
-                s[at] = CLASS_BYTES[rng.integers(0, CLASS_BYTES.size)]
-            strings.append(s)
-        offsets = synth.offsets_of([x.size for x in strings])
-        data = np.concatenate(strings)
+        offsets = synth.offsets_of(lens)
+        data = synth.fill_strings(offsets, synth.UNIFORM, seed=shift + 29).copy()
+        # 30% of the non-empty strings get one byte replaced: in their first
+        # three bytes, their last three or anywhere
+        starts, n = offsets[:-1], lens
+        hit = (n > 0) & (rng.random(n.size) < 0.3)
+        kind = rng.integers(0, 3, n.size)
+        r = rng.integers(0, 1 << 30, n.size)
+        near = r % np.minimum(np.maximum(n, 1), 3)
+        rel = np.where(kind == 0, near, np.where(kind == 1, n - 1 - near, r % np.maximum(n, 1)))
+        at = (starts + rel)[hit]
+        data[at] = CLASS_BYTES[rng.integers(0, CLASS_BYTES.size, at.size)]
         shifted = np.concatenate([np.full(shift, 0x41, np.uint8), data])
         want = oracle.valid_batch(data, offsets)
         assert (want == 0).mean() > 0.1
