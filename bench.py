@@ -3,18 +3,24 @@
 
 Workload (one step): the five 1 GiB seeded content variants (pure ASCII,
 Latin-like, CJK-like, emoji-heavy, uniform 1-4 byte mix) plus a copy of each
-whose last 3 bytes hold a truncated character: ten 1 GiB buffers, each
-validated by one utf8_validate_async call (a 1-byte memset and one
-validate_kernel launch) on one stream.  Inputs are resident in HBM before the
-timed region; each buffer is larger than the 129 MB L2, so nothing is served
-from L2 across iterations.
+whose last 3 bytes hold a truncated character: ten independent 1 GiB
+buffers, validated by one utf8_validate_buffers_async call (two small
+memsets and one buffers_kernel launch, which checks every buffer exactly as
+a single-buffer call would while interleaving their chunks) on one stream.
+The same buffers are also timed through ten single-buffer calls
+(utf8_validate_async, one after the other) and reported beside it.  Inputs
+are resident in HBM before the timed region; each buffer is larger than the
+129 MB L2, so nothing is served from L2 across iterations.
 
 Metric: validated GB/s (1e9 input bytes per second), whole job.  Beside it:
-% of the measured HBM copy peak, the kernel roofline, the end-to-end rate of
-the host-memory entry point (pinned host buffers copied in every step), the
-oracle on the host cores (a bounded sample), and two secondary measurements:
-the 1M-string batch against launching one validation per string, and the
-serving loop's latency percentiles.
+% of the measured HBM copy peak, the kernel rooflines (HBM, and the integer
+ALU for the classifying single-buffer launches), the end-to-end rate of the
+host-memory entry point (pinned host buffers copied in every step), the
+oracle on the host cores (a bounded sample), and secondary measurements:
+the 1 MiB config's latencies, error location, the paper's finite-state
+validator on the GPU, the 1M-string batch against launching one validation
+per string, streaming, copy + validate, and the serving loop's latency
+percentiles.
 
 --impl reference times the CPU oracle (the only reference that exists for
 this method) on the same workload, a bounded sample per step.
@@ -50,8 +56,8 @@ METRIC = "validated GB/s"
 # pairs.  Used only when no ncu count taken on the current kernel sources is
 # on record in profiles/traffic.json.
 ALU_OPS_PER_BYTE_DESIGN = (28 + 2 / 16) / 8
-WORKLOAD = ("single 1 GiB buffers: 5 seeded content variants (ascii, latin, cjk, emoji, "
-            "uniform 1-4 byte) + a truncated-tail copy of each = 10 GiB per step")
+WORKLOAD = ("ten independent 1 GiB buffers: 5 seeded content variants (ascii, latin, cjk, "
+            "emoji, uniform 1-4 byte) + a truncated-tail copy of each = 10 GiB per step")
 
 
 def parse_args():
@@ -62,7 +68,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--buffer-bytes", type=int, default=GIB)
     ap.add_argument("--no-extras", action="store_true", help="skip batch/serving extras")
-    ap.add_argument("--legs", default="main,e2e,cpu,alu,cfg1mib,locate,fsm,batch,serve,stream,copy,small",
+    ap.add_argument("--legs", default="main,single,e2e,cpu,alu,cfg1mib,locate,fsm,batch,serve,stream,copy,small",
                     help="comma-separated legs to run (profiling runs pick one)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-memory leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
@@ -187,16 +193,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_traffic(kernel: str, rows: int):
+def kernel_traffic(kernel: str, rows: int, files=("lookup.cuh", "tiles.cuh", "validate.cu")):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (same hash) and tile height; None otherwise."""
+    on the current kernel sources (same hash of `files`) and tile height;
+    None otherwise."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f).get(kernel)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("source_hash") != source_hash() or rec.get("rows") != rows:
+    if not rec or rec.get("source_hash") != source_hash(files) or rec.get("rows") != rows:
         return None
     return rec
 
@@ -419,13 +426,16 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     bytes_per_step = sum(b.size for b in host)
     u.lib()
 
+    # one step: the ten buffers through one utf8_validate_buffers_async call
+    # (two memsets and one buffers_kernel launch, chunks interleaved across
+    # the buffers, so HBM-bound ASCII buffers and ALU-bound non-ASCII ones
+    # run side by side)
     def step(events=None, k=0):
-        for i, t in enumerate(dev):
-            if events is not None:
-                events[k][i][0].record(stream)
-            u.utf8_validate_async(t, res[i:i + 1], stream=stream)
-            if events is not None:
-                events[k][i][1].record(stream)
+        if events is not None:
+            events[k][0].record(stream)
+        u.utf8_validate_buffers_async(dev, res, stream=stream)
+        if events is not None:
+            events[k][1].record(stream)
 
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
@@ -433,8 +443,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     stream.synchronize()
     flags = res.cpu().numpy().tolist()
 
-    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in dev] for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local_rank)
     if dist:
@@ -451,8 +461,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     torch.cuda.synchronize()
     clock_info = clocks.stop()
     elapsed_ms = max_over_ranks(start.elapsed_time(stop), dist, "cuda")
-    per_buf_ms = np.array([[a.elapsed_time(b) for a, b in row] for row in ev])
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
     value = whole_job_gbs(world, bytes_per_step, args.steps, elapsed_ms)
+    # the same buffers through ten single-buffer calls (utf8_validate_async),
+    # one after the other: each buffer's own rate, and the ALU roofline
+    single = (bench_single_calls(u, torch, dev, names, stream, max(20, args.steps // 4))
+              if "single" in legs else None)
 
     # end to end, on every rank at once: host buffers through the public
     # host-memory entry point; all ranks' bytes over the slowest rank's time
@@ -483,24 +497,29 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     peaks = measured_peaks()
     peak = float(peaks.get("hbm_gbs") or FALLBACK_HBM_GBS)
-    # HBM roofline of validate_kernel: algorithmic bytes (the input, 1 B/B)
-    # per launch over the launch's average event time (1-byte memset + kernel)
-    launch_ms = float(per_buf_ms.mean())
-    achieved = n / (launch_ms / 1e3) / 1e9
+    # HBM roofline of buffers_kernel, the step's one kernel: algorithmic
+    # bytes (the input, 1 B/B: ten buffers) per launch over the launch's
+    # average event time (two small memsets + the kernel)
+    launch_ms = float(step_ms.mean())
+    achieved = bytes_per_step / (launch_ms / 1e3) / 1e9
     cfg = json.loads(u.utf8_config_json())
-    traffic = kernel_traffic("validate_kernel", int(cfg["rows"]))
-    # integer-ALU roofline of the launches that classify (non-ASCII content):
-    # ops per byte counted by ncu on the current sources (else the design
-    # count), against the probe's measured ALU-pipe rate x SMs x SM clock
+    traffic = kernel_traffic("buffers_kernel", int(cfg["rows"]),
+                             ("lookup.cuh", "tiles.cuh", "buffers.cu"))
+    # integer-ALU roofline of the single-buffer launches that classify
+    # (non-ASCII content): ops per byte counted by ncu on the current sources
+    # (else the design count), against the probe's measured ALU-pipe rate x
+    # SMs x SM clock
+    v_traffic = kernel_traffic("validate_kernel", int(cfg["rows"]))
     cls = [i for i, nm in enumerate(names) if not nm.startswith("ascii")]
     sm_count = int(cfg.get("sm_count", 152))
-    sm_mhz = clock_info.get("sm_mhz") or float(peaks.get("sm_max_mhz") or 2070.0)
+    sm_mhz = clock_info.get("sm_mhz") or float(peaks_mhz_default())
     probe = alu_probe(sm_mhz) if "alu" in legs else {}
     alu_rate = min(probe.get(k, 0.0) for k in ("lop3", "prmt", "shf")) if "lop3" in probe else None
-    ops_b = traffic.get("alu_ops_per_byte") if traffic else None
+    ops_b = v_traffic.get("alu_ops_per_byte") if v_traffic else None
+    per_buf_ms = single["per_buf_ms"] if single else None
     alu_roofline = None
-    if cls:
-        cls_bytes = sum(host[i].size for i in cls) * args.steps
+    if cls and single:
+        cls_bytes = sum(host[i].size for i in cls) * per_buf_ms.shape[0]
         cls_s = per_buf_ms[:, cls].sum() / 1e3
         cls_gbs = cls_bytes / cls_s / 1e9
         ops = ops_b or ALU_OPS_PER_BYTE_DESIGN
@@ -508,7 +527,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         alu_peak = sm_count * lanes * sm_mhz * 1e6 / 1e9  # Gop/s
         alu_achieved = cls_gbs * ops
         alu_roofline = {
-            "bound": "alu", "kernel": "validate_kernel (non-ASCII launches)",
+            "bound": "alu", "kernel": "validate_kernel (single-buffer calls, non-ASCII launches)",
             "achieved": round(alu_achieved, 1), "peak": round(alu_peak, 1), "unit": "Gop/s",
             "frac": round(alu_achieved / alu_peak, 4),
             "ops_per_byte": round(ops, 3),
@@ -519,8 +538,22 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                             if alu_rate else f"nominal 64 ops/clk/SM x {sm_count} SMs x "
                                              f"{sm_mhz:.0f} MHz"),
             "validated_gbs": round(cls_gbs, 1), "probe": probe or None}
-    per_variant = {nm: round(host[i].size / (per_buf_ms[:, i].mean() / 1e3) / 1e9, 1)
-                   for i, nm in enumerate(names)}
+    single_line = None
+    if single:
+        v_launch_ms = float(per_buf_ms.mean())
+        v_achieved = n / (v_launch_ms / 1e3) / 1e9
+        single_line = {
+            "api": "utf8_validate_async, one call per buffer, one after the other",
+            "gbs": single["gbs"], "pct_of_hbm_peak": round(100 * single["gbs"] / peak, 1),
+            "steps": int(per_buf_ms.shape[0]),
+            "per_variant_gbs": {nm: round(host[i].size / (per_buf_ms[:, i].mean() / 1e3) / 1e9, 1)
+                                for i, nm in enumerate(names)},
+            "roofline": {"bound": "hbm", "kernel": "validate_kernel",
+                         "achieved": round(v_achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(v_achieved / peak, 4),
+                         "traffic": v_traffic["dram_bytes_per_launch"] if v_traffic else None,
+                         "algorithmic_bytes_per_launch": n, "launch_ms": round(v_launch_ms, 4)},
+            "flags_match": single["flags"] == flags}
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
@@ -529,28 +562,30 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (seeded generators; the paper's files are not available)",
         "config": {"workload": WORKLOAD, "bytes_per_step": bytes_per_step,
+                   "api": "utf8_validate_buffers_async: the ten buffers in one call",
                    "l2": "inputs larger than L2 (each buffer 1 GiB > 129 MB L2)",
                    "launch": cfg},
         "pct_of_hbm_peak": {"measured": round(100 * value / world / peak, 1),
                             "nominal_8000": round(100 * value / world / NOMINAL_HBM_GBS, 1)},
-        "roofline": {"bound": "hbm", "kernel": "validate_kernel",
+        "roofline": {"bound": "hbm", "kernel": "buffers_kernel",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
                      "peak_source": ("measured (MEASURED_PEAKS.json hbm_gbs, burst copy)"
                                      if peaks.get("hbm_gbs") else "fallback 6800 GB/s"),
                      "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
-                     "algorithmic_bytes_per_launch": n,
+                     "algorithmic_bytes_per_launch": bytes_per_step,
                      "launch_ms": round(launch_ms, 4),
-                     "timing": "CUDA events around each launch (1-byte memset + kernel) on "
-                               "the launching stream, averaged over the timed region"},
+                     "timing": "CUDA events around each utf8_validate_buffers_async call (two "
+                               "small memsets + the kernel) on the launching stream, averaged "
+                               "over the timed region"},
         "alu_roofline": alu_roofline,
-        "per_variant_gbs": per_variant,
+        "single_buffer_calls": single_line,
         "flags": dict(zip(names, flags)),
         "e2e": {"value": round(e2e_value, 1) if e2e_value else None, "unit": "GB/s",
                 "h2d_bytes_per_step": bytes_per_step, "d2h_bytes_per_step": len(host),
                 "steps": e2e_steps, "api": "utf8_validate_host (pinned host buffers)",
                 "flags_ok": [bool(f) for f in e2e_flags] == [bool(f) for f in flags]},
-        "gpu_launches": len(dev) * args.steps,
+        "gpu_launches": args.steps,
         "clocks": clock_info,
     }
     if world == 1 and "cpu" in legs:
@@ -579,6 +614,36 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def peaks_mhz_default() -> float:
+    return float(measured_peaks().get("sm_max_mhz") or 2070.0)
+
+
+def bench_single_calls(u, torch, dev, names, stream, steps: int) -> dict:
+    """The main leg's buffers through one utf8_validate_async call each (a
+    1-byte memset and one validate_kernel launch per buffer), one after the
+    other; CUDA events around every call."""
+    res = torch.empty(len(dev), dtype=torch.uint8, device="cuda")
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in dev] for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            for i, t in enumerate(dev):
+                u.utf8_validate_async(t, res[i:i + 1], stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for k in range(steps):
+            for i, t in enumerate(dev):
+                ev[k][i][0].record(stream)
+                u.utf8_validate_async(t, res[i:i + 1], stream=stream)
+                ev[k][i][1].record(stream)
+        b.record(stream)
+    stream.synchronize()
+    total = sum(t.numel() for t in dev) * steps
+    return {"gbs": round(total / (a.elapsed_time(b) / 1e3) / 1e9, 1),
+            "per_buf_ms": np.array([[x.elapsed_time(y) for x, y in row] for row in ev]),
+            "flags": res.cpu().numpy().tolist()}
 
 
 def bench_locate(u, torch, dev, names, stream, flags=None, steps: int = 30) -> dict:

@@ -73,6 +73,27 @@ int utf8_validate_async(const uint8_t* data, size_t len, uint8_t* out_valid,
                         cudaStream_t stream);
 
 /*
+ * Many independent device buffers in one launch: out_valid[i] = 1 iff
+ * data[i][0 .. lens[i]) is valid UTF-8, each buffer checked exactly as
+ * utf8_validate checks it (Section 6).  data, lens: host arrays of `count`
+ * entries (read during the call; a buffer with lens[i] == 0 may be NULL and
+ * is valid); out_valid: device uint8[count].  The buffers' tiles are cut
+ * into 128 KiB chunks interleaved across the buffers and taken by the warps
+ * from a counter, so buffers bound by HBM bandwidth (ASCII text) and
+ * buffers bound by the integer ALU (the classification of non-ASCII text)
+ * are checked at the same time rather than one after the other.  Up to 64
+ * buffers go in one launch; more are split into launches of 64.  Each
+ * launch uses one of 1024 counters the library keeps per device (zeroed on
+ * the stream before the launch): at most 1024 of these calls may run on
+ * the GPU at once, and a CUDA graph holding this call must not be replayed
+ * while it is still running.  Asynchronous, no allocation; returns a status
+ * (UTF8_ERR_INVALID_ARG for count < 0, a null array, or a pointer that is
+ * not device memory).
+ */
+int utf8_validate_buffers_async(const uint8_t* const* data, const size_t* lens, int count,
+                                uint8_t* out_valid, cudaStream_t stream);
+
+/*
  * The paper's finite-state validator (Section 5: nine states, the continuation
  * ranges 80..8F / 90..9F / A0..BF, one transition per byte) on the GPU, for
  * comparison with the `lookup` path of utf8_validate_async; same arguments,

@@ -23,6 +23,7 @@ from ._lib import (  # noqa: F401
     utf8_validate,
     utf8_validate_async,
     utf8_validate_fsm_async,
+    utf8_validate_buffers_async,
     utf8_validate_batch,
     utf8_validate_host,
     utf8_validate_host_noalloc,

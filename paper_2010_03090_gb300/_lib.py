@@ -20,7 +20,7 @@ EXPORTS = (
     "utf8_stream_update", "utf8_stream_finish", "utf8_stream_destroy", "utf8_copy_validate",
     "utf8_locate_error", "utf8_locate_error_async", "utf8_locate_errors_batch",
     "utf8_check_offsets", "utf8_validate_batch_desc", "utf8_set_early_exit",
-    "utf8_validate_fsm_async",
+    "utf8_validate_fsm_async", "utf8_validate_buffers_async",
 )
 
 # Section 3's rules a-f as the library numbers them (enum utf8_rule).
@@ -59,6 +59,8 @@ def lib() -> ctypes.CDLL:
             L.utf8_validate_async.restype = i32
             L.utf8_validate_fsm_async.argtypes = [vp, sz, vp, vp]
             L.utf8_validate_fsm_async.restype = i32
+            L.utf8_validate_buffers_async.argtypes = [vp, vp, i32, vp, vp]
+            L.utf8_validate_buffers_async.restype = i32
             L.utf8_validate_batch.argtypes = [vp, vp, i64, vp, vp]
             L.utf8_validate_batch.restype = i32
             L.utf8_validate_host.argtypes = [vp, sz, vp]
@@ -164,6 +166,27 @@ def utf8_validate_async(data, out_valid=None, stream=None):
     q, _ = _dev(out_valid, "uint8", "out_valid")
     _check(lib().utf8_validate_async(p or None, n, q, _stream(stream)), "utf8_validate_async")
     return out_valid
+
+
+def utf8_validate_buffers_async(buffers, out_valid=None, stream=None):
+    """Queues the validation of a list of uint8 CUDA tensors in one launch;
+    returns a uint8 CUDA tensor with one flag per buffer (1 = valid)."""
+    import torch
+    n = len(buffers)
+    ptrs = (ctypes.c_void_p * max(n, 1))()
+    lens = (ctypes.c_size_t * max(n, 1))()
+    for i, t in enumerate(buffers):
+        p, m = _dev(t, "uint8", "buffers[%d]" % i)
+        ptrs[i], lens[i] = p or None, m
+    if out_valid is None:
+        dev = buffers[0].device if n else "cuda"
+        out_valid = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+    q, k = _dev(out_valid, "uint8", "out_valid")
+    if k < n:
+        raise ValueError("out_valid is too small")
+    _check(lib().utf8_validate_buffers_async(ptrs, lens, n, q, _stream(stream)),
+           "utf8_validate_buffers_async")
+    return out_valid[:n]
 
 
 def utf8_validate_fsm_async(data, out_valid=None, stream=None):

@@ -32,6 +32,7 @@ inline int set_status(int s) {
 constexpr int kMaxDevices = 64;
 constexpr uint32_t kResultSlots = 4096;
 constexpr uint32_t kInfoSlots = 1024;  // utf8_error_info slots of utf8_locate_error
+constexpr uint32_t kChunkCounters = 1024;  // work counters of utf8_validate_buffers_async
 constexpr uint64_t kStageChunk = 64ull << 20;   // bytes per pipelined host copy
 constexpr uint64_t kStageWindow = 4ull << 30;   // largest staging buffer
 constexpr int kStageEvents = 64;
@@ -58,6 +59,10 @@ struct DeviceState {
   uint8_t* dm_results = nullptr;  // the device address of h_results
   std::atomic<uint32_t> next_slot{0};
   utf8_error_info* d_info = nullptr;  // kInfoSlots error locations
+  // kChunkCounters device counters from which the warps of a multi-buffer
+  // launch take their chunks; each launch takes the next one and zeroes it
+  unsigned* d_counters = nullptr;
+  std::atomic<uint32_t> next_counter{0};
   utf8_error_info* h_info = nullptr;  // pinned mirror
   std::atomic<uint32_t> next_info{0};
   // host-memory path
@@ -83,6 +88,7 @@ void init_device(DeviceState& d, int dev) {
   if (e == cudaSuccess)
     e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&d.dm_results), d.h_results, 0);
   if (e == cudaSuccess) e = cudaMalloc(&d.d_info, kInfoSlots * sizeof(utf8_error_info));
+  if (e == cudaSuccess) e = cudaMalloc(&d.d_counters, kChunkCounters * sizeof(unsigned));
   if (e == cudaSuccess)
     e = cudaHostAlloc(&d.h_info, kInfoSlots * sizeof(utf8_error_info), cudaHostAllocDefault);
   d.init_error = e;
@@ -203,6 +209,28 @@ int utf8_validate_async(const uint8_t* data, size_t len, uint8_t* out_valid,
     return set_status(UTF8_ERR_INVALID_ARG);
   if (len == 0) return cuda_status(cudaMemsetAsync(out_valid, 1, 1, stream));
   return cuda_status(launch_validate(data, len, out_valid, config_of(*d), d->sm_count, stream));
+}
+
+int utf8_validate_buffers_async(const uint8_t* const* data, const size_t* lens, int count,
+                                uint8_t* out_valid, cudaStream_t stream) {
+  if (count < 0 || (count > 0 && (data == nullptr || lens == nullptr || out_valid == nullptr)))
+    return set_status(UTF8_ERR_INVALID_ARG);
+  if (count == 0) return set_status(UTF8_OK);
+  DeviceState* d = device();
+  if (!d) return UTF8_ERR_CUDA;
+  if (!is_device_memory(out_valid)) return set_status(UTF8_ERR_INVALID_ARG);
+  for (int i = 0; i < count; ++i)
+    if (lens[i] > 0 && (data[i] == nullptr || !is_device_memory(data[i])))
+      return set_status(UTF8_ERR_INVALID_ARG);
+  const LaunchCfg cfg = config_of(*d);
+  for (int first = 0; first < count; first += kMaxBuffersPerLaunch) {
+    const int n = count - first < kMaxBuffersPerLaunch ? count - first : kMaxBuffersPerLaunch;
+    unsigned* next = d->d_counters + d->next_counter.fetch_add(1) % kChunkCounters;
+    const cudaError_t e = launch_buffers(data + first, lens + first, n, out_valid + first, next,
+                                         cfg, d->sm_count, stream);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return set_status(UTF8_OK);
 }
 
 int utf8_validate_fsm_async(const uint8_t* data, size_t len, uint8_t* out_valid,

@@ -39,6 +39,15 @@ cudaError_t preload_validate_kernels();
 bool early_exit_enabled();
 int set_early_exit(int enable);  // returns the previous setting (0 or 1)
 
+// Independent buffers in one launch, chunks interleaved across them and taken
+// from the device counter *next (buffers.cu); sets out_valid[0 .. count) to 1
+// and *next to 0 on the stream first.  count <= kMaxBuffersPerLaunch.
+constexpr int kMaxBuffersPerLaunch = 64;
+constexpr uint64_t kBuffersChunkBytes = 128 << 10;
+cudaError_t launch_buffers(const uint8_t* const* data, const size_t* lens, int count,
+                           uint8_t* out_valid, unsigned* next, const LaunchCfg& cfg,
+                           int sm_count, cudaStream_t st);
+
 // The paper's finite-state validator (Section 5) over one buffer (fsm.cu);
 // the result byte must hold 1 before the launch.
 cudaError_t launch_validate_fsm(const uint8_t* data, uint64_t n, uint8_t* out_valid, int sm_count,
