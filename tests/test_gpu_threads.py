@@ -1,6 +1,6 @@
 """Entry points called from many host threads at once (the header promises
 thread safety): each thread uses its own stream and mixes the synchronous,
-asynchronous, error-location, host-memory and batch calls on valid and
+asynchronous, error-location, host-memory, batch and multi-buffer calls on valid and
 invalid buffers, while another thread retunes the launch configuration.
 Every result must equal the oracle's.  Needs a GPU."""
 import json
@@ -52,9 +52,10 @@ def test_concurrent_calls_from_host_threads():
             s = torch.cuda.Stream()
             out = torch.empty(1, dtype=torch.uint8, device="cuda")
             flags = torch.empty(len(strings), dtype=torch.uint8, device="cuda")
+            three = torch.empty(3, dtype=torch.uint8, device="cuda")
             for it in range(40):
                 k = (t * 7 + it) % len(bufs)
-                mode = (t + it) % 5
+                mode = (t + it) % 6
                 if mode == 0:
                     got = u.utf8_validate(dev[k], stream=s)
                     ok = got == want[k]
@@ -66,10 +67,15 @@ def test_concurrent_calls_from_host_threads():
                     ok = u.utf8_locate_error(dev[k], stream=s) == where[k]
                 elif mode == 3:
                     ok = u.utf8_validate_host(pinned[k], stream=s) == want[k]
-                else:
+                elif mode == 4:
                     u.utf8_validate_batch(d_data, d_off, flags, stream=s)
                     s.synchronize()
                     ok = np.array_equal(flags.cpu().numpy(), want_batch)
+                else:
+                    ks = [(k + j) % len(bufs) for j in range(3)]
+                    u.utf8_validate_buffers_async([dev[j] for j in ks], three, stream=s)
+                    s.synchronize()
+                    ok = three.cpu().numpy().tolist() == [int(want[j]) for j in ks]
                 if not ok:
                     failures.append((t, it, k, mode))
         except Exception as e:  # noqa: BLE001
