@@ -48,14 +48,15 @@ NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6800.0
 METRIC = "validated GB/s"
 # Integer ALU-pipe operations (LOP3, PRMT, SHF) per byte of non-ASCII text,
-# as the kernel's design counts them for one 8-byte interleaved pair:
-# selectors 7 (one right shift, 3 bit selects, 3 half-word shifts), table
-# lookups 10 and their AND 2, the checks 8 (per word: two funnel shifts, the
-# expectation mask and the error XOR) and the error fold 1: 28 (8 SHF, 10
-# PRMT, 10 LOP3), plus the tile's all-ASCII test on its first row, 2 per 16
-# pairs.  Used only when no ncu count taken on the current kernel sources is
-# on record in profiles/traffic.json.
-ALU_OPS_PER_BYTE_DESIGN = (28 + 2 / 16) / 8
+# as the kernel's design counts them for one 16-byte column of a row quad
+# (four words, one byte of each of four rows per word): selectors 18 (two
+# right shifts, 4 bit selects, 8 byte-permute gathers, 4 complements), table
+# lookups 20 and their AND 4, the checks 8 (per word: the expectation mask and
+# the error XOR) and the error fold 2: 52 (2 SHF, 28 PRMT, 22 LOP3).  A lane's
+# share of a 4 KiB tile is 8 such columns, plus 4 carry merges per quad and
+# the all-ASCII test on the tile's first row (2).  Used only when no ncu count
+# taken on the current kernel sources is on record in profiles/traffic.json.
+ALU_OPS_PER_BYTE_DESIGN = (8 * 52 + 2 * 4 + 2) / 128
 WORKLOAD = ("ten independent 1 GiB buffers: 5 seeded content variants (ascii, latin, cjk, "
             "emoji, uniform 1-4 byte) + a truncated-tail copy of each = 10 GiB per step")
 

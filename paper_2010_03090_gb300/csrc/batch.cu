@@ -97,6 +97,12 @@ __device__ void warp_lower_bound2(const int64_t* offsets, int64_t hi, int64_t ta
   res_b = lb_final(lo_b, hi_b, mask_b);
 }
 
+// The batch pass classifies its tiles as row pairs, not quads (tiles.cuh):
+// with quads its staging, boundary and charging state needs 169 registers, so
+// one CTA fits an SM, and the 1M-string batch ran 2.6% slower (1.4% slower
+// with quads at 4-row tiles, which fit two CTAs).
+constexpr bool kBatchQuads = false;
+
 // An error at `rel` bytes into string j: its flag is cleared, or (LOCATE) its
 // first erroneous position is lowered to rel (see locate.cuh).
 template <bool LOCATE>
@@ -147,10 +153,10 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
   uint32_t* err_words = stage + 4;
   static_assert(ROWS / 2 * 8 * kLanes == ROWS * kLanes * 4, "error words fit the tile part");
 
-  const uint32_t merge_sel = carry_merge_selector(lane);
+  const uint32_t merge_sel = carry_merge_selector<kBatchQuads>(lane);
   Carry carry = ascii_carry();
   const uint32_t halo = t0 > 0 ? load_word(region, t0 * kTileBytes - 4) : 0u;
-  if (t0 > 0) carry = halo_carry(halo);
+  if (t0 > 0) carry = halo_carry<kBatchQuads>(halo);
   if (lane == 0) {
     stage[2] = t0 > 0 ? load_word(region, t0 * kTileBytes - 8) : 0u;
     stage[3] = halo;
@@ -238,7 +244,7 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
     take_windows(tile_lo, true);
     bool staged = true;  // the stage still holds this tile
     uint32_t e[ROWS / 2][8];
-    check_tile<ROWS>(d, carry, lane, merge_sel, e);
+    check_tile<ROWS, kBatchQuads>(d, carry, lane, merge_sel, e);
     uint32_t any_err = 0;
 #pragma unroll
     for (int p = 0; p < ROWS / 2; ++p)
@@ -278,11 +284,13 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
         int64_t p = INT64_MAX;
         if (bits != 0) {
           const int byte = (__ffs(bits) - 1) >> 3;
-          // bytes `byte` and byte + 2 are positions 2m and 2m+1 of one row:
-          // the first decides for both (the same string, or 2m+1 starts one,
-          // and a string's first three bytes are the head check's)
+          // row pairs: bytes `byte` and byte + 2 are positions 2m and 2m+1
+          // of one row, and the first decides for both (the same string, or
+          // 2m+1 starts one, and a string's first three bytes are the head
+          // check's); in a quad word every byte is a row of its own
+          static_assert(!kBatchQuads, "the pair rule below");
           bits &= ~(0x00FF00FFu << (8 * byte));
-          p = tile_lo + (int64_t)interleaved_position<ROWS>(k >> 3, k & 7, byte, lane);
+          p = tile_lo + (int64_t)interleaved_position<ROWS, kBatchQuads>(k >> 3, k & 7, byte, lane);
         }
         uint32_t pending = __ballot_sync(kFull, p != INT64_MAX);
         if (pending == 0) break;

@@ -36,7 +36,7 @@ struct BuffersArgs {
 };
 
 template <int ROWS>
-__global__ void __launch_bounds__(kBlockThreads) buffers_kernel(BuffersArgs a, unsigned* next,
+__global__ void __launch_bounds__(kBlockThreads, 2) buffers_kernel(BuffersArgs a, unsigned* next,
                                                                uint8_t* out_valid) {
   const int lane = threadIdx.x & (kLanes - 1);
   const uint32_t total = a.seg_chunk[a.segments];

@@ -52,9 +52,9 @@ __global__ void __launch_bounds__(kBlockThreads)
   const uint64_t t0 = tiles * w / warps;
   const uint64_t t1 = tiles * (w + 1) / warps;
   if (t0 >= t1) return;
-  const uint32_t merge_sel = carry_merge_selector(lane);
+  const uint32_t merge_sel = carry_merge_selector<kQuadRows<ROWS>>(lane);
   Carry carry = ascii_carry();
-  if (t0 > 0) carry = halo_carry(load_word(s, t0 * tb - 4));
+  if (t0 > 0) carry = halo_carry<kQuadRows<ROWS>>(load_word(s, t0 * tb - 4));
   uint64_t in0, in1;
   interior_tiles<ROWS>(s, in0, in1);
   const uint8_t* lane_ptr = s.abase + t0 * tb + lane * 16;

@@ -40,9 +40,12 @@
 //    low nibble (entries 0..7, sign mode gives 0xFF for 8..F) AND-ed with a
 //    lookup through the complemented low nibble (entries 8..F, 0xFF for 0..7)
 //    gives the table exactly.
-//  * The previous-byte lookups are computed on the current bytes, then moved
-//    to the next position by a funnel shift (the paper's prev<1>), so each
-//    byte is looked up once.
+//  * The previous-byte lookups are computed on the current bytes and used at
+//    the next position (the paper's prev<1>), so each byte is looked up once.
+//    The kernels classify four rows of a tile side by side, one byte of each
+//    row per word (lut_quad): the previous bytes of a word are then the
+//    previous word itself, with no shift at all.  Two rows side by side
+//    (lut_interleaved) need a 16-bit funnel shift.
 //
 // A position is an error iff its byte  ((prev side of byte i-1) & (current
 // side of byte i)) ^ (expectation of byte i)  is non-zero; it has no bits
@@ -218,6 +221,27 @@ __device__ __forceinline__ void lut_interleaved(uint32_t c, uint32_t d, WordLut&
   const uint32_t lo_c = bit_select_not(c, d << 4, lo_mask);
   A = lut_from_selectors(hi_c, lo, lo_c);
   B = lut_from_selectors(hi_c >> 16, lo >> 16, lo_c >> 16);
+}
+
+// Lookups for byte column 4t..4t+3 of four streams a, b, c, d (natural words),
+// as four words W_j = (a_j, b_j, c_j, d_j), j = 0..3: each word holds one
+// byte position of the four streams, so the previous bytes of W_j are the
+// word before it.  The nibbles of two streams are packed per byte by one
+// select each; one byte permute per selector then gathers byte j of both
+// packs into the low 16 bits.
+__device__ __forceinline__ void lut_quad(uint32_t a, uint32_t b, uint32_t c, uint32_t d,
+                                         WordLut (&W)[4]) {
+  const uint32_t lo_mask = 0x0F0F0F0Fu;
+  const uint32_t hab = bit_select_not(a >> 4, b, lo_mask);  // byte j: ~(a_j.hi | b_j.hi << 4)
+  const uint32_t hcd = bit_select_not(c >> 4, d, lo_mask);
+  const uint32_t lab = bit_select(a, b << 4, lo_mask);      // byte j: a_j.lo | b_j.lo << 4
+  const uint32_t lcd = bit_select(c, d << 4, lo_mask);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t sel = (uint32_t)(j | ((4 + j) << 4));
+    const uint32_t lo = prmt(lab, lcd, sel);
+    W[j] = lut_from_selectors(prmt(hab, hcd, sel), lo, ~lo);
+  }
 }
 
 // The expectation terms of two bytes back and three back, folded per byte:

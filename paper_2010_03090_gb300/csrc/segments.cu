@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     const uint64_t b = (t1 < end ? t1 : end) - base;
     if (a >= b) continue;
     const Span s = make_span(segs[i].data, segs[i].len);
-    const uint32_t err = warp_check_tiles<ROWS>(s, a, b);
+    const uint32_t err = warp_check_tiles<ROWS, false>(s, a, b);
     if (__any_sync(kFull, err != 0) && lane == 0) clear_result(out_valid + i);
   }
 }

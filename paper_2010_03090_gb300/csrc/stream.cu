@@ -49,7 +49,7 @@ __device__ __forceinline__ void mask_positions(uint32_t (&e)[ROWS / 2][8], uint6
     for (int m = 0; m < 8; ++m)
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        const uint64_t v = tile_v + interleaved_position<ROWS>(p, m, b, lane);
+        const uint64_t v = tile_v + interleaved_position<ROWS, false>(p, m, b, lane);
         if (v < lo || v >= hi) e[p][m] &= ~(0xFFu << (8 * b));
       }
 }
@@ -75,13 +75,13 @@ __global__ void __launch_bounds__(kBlockThreads) chunk_kernel(Span s, uint64_t t
   const uint64_t t0 = tiles * w / warps;
   const uint64_t t1 = tiles * (w + 1) / warps;
   if (t0 >= t1) return;
-  const uint32_t merge_sel = carry_merge_selector(lane);
+  const uint32_t merge_sel = carry_merge_selector<false>(lane);
   Carry carry;
   if (t0 == 0) {
     // virtual bytes -4..-1 are data offsets -4-off .. -1-off
-    carry = halo_carry(s.off < 4 ? pre << (8 * s.off) : 0u);
+    carry = halo_carry<false>(s.off < 4 ? pre << (8 * s.off) : 0u);
   } else {
-    carry = halo_carry(load_word(s, t0 * tb - 4));
+    carry = halo_carry<false>(load_word(s, t0 * tb - 4));
   }
   const uint64_t keep_hi = a.final_chunk ? ~uint64_t(0) : s.off + s.n;
   uint64_t in0, in1;
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kBlockThreads) chunk_kernel(Span s, uint64_t t
       }
     }
     uint32_t e[ROWS / 2][8];
-    check_tile<ROWS>(d, carry, lane, merge_sel, e);
+    check_tile<ROWS, false>(d, carry, lane, merge_sel, e);
     const uint64_t tile_v = t * tb;
     if (tile_v < s.off || tile_v + tb > keep_hi) mask_positions<ROWS>(e, tile_v, lane, s.off, keep_hi);
 #pragma unroll

@@ -94,33 +94,50 @@ __device__ __forceinline__ uint32_t load_word(const Span& s, uint64_t v) {
   return w & keep_bytes(a, b);
 }
 
-// What lane 0 of a row pair needs from the row pair before it: the last
-// interleaved word W_7 of lane 31 (the last four bytes of both rows): its
-// prev_side, its flags and its back23 (see lookup.cuh).  Only the
-// second-stream bytes (1 and 3) are used.
+// What lane 0 of a row group needs from the row group before it: lookups of
+// the last word of lane 31 (the last bytes of every row).
+//  * Row pairs: interleaved word W_7 (the last four bytes of both rows): its
+//    prev_side, flags and back23 in p, f and hb; the second-stream bytes (1
+//    and 3) are used.
+//  * Row quads: word W_15 (byte 15 of the four rows): its prev_side and flags
+//    in p and f, back23 of W_14 and W_15 in ha and hb; byte 3 (the quad's last
+//    row) is used.
 struct Carry {
-  uint32_t x7;  // prev_side of W_7
-  uint32_t f7;  // flags of W_7
-  uint32_t h7;  // back23 of W_7
+  uint32_t p;
+  uint32_t f;
+  uint32_t ha;
+  uint32_t hb;
 };
+
+// Rows are classified four at a time when the tile height allows it (see
+// check_tile); a kernel may ask for row pairs instead.
+template <int ROWS>
+constexpr bool kQuadRows = ROWS % 4 == 0;
 
 __device__ __forceinline__ Carry ascii_carry() {
   const WordLut a = ascii_lut();
-  return Carry{a.prev_side, a.flags, 0u};
+  return Carry{a.prev_side, a.flags, 0u, 0u};
 }
 
 // Carry for a stream whose previous four bytes (natural order) are `halo`.
+template <bool QUADS>
 __device__ __forceinline__ Carry halo_carry(uint32_t halo) {
   const WordLut h = lut_word(halo);
-  return Carry{prmt(h.prev_side, 0, 0x3020), prmt(h.flags, 0, 0x3020),
-               prmt(back23_word(h), 0, 0x3020)};
+  const uint32_t b = back23_word(h);  // byte k: back23 of halo byte k (k = 2, 3 exact)
+  if constexpr (QUADS) return Carry{h.prev_side, h.flags, b << 8, b};
+  return Carry{prmt(h.prev_side, 0, 0x3020), prmt(h.flags, 0, 0x3020), 0u, prmt(b, 0, 0x3020)};
 }
 
 // Error bytes of the first four positions of a tile's row 0 (natural order,
 // word w) after the carry: the check an all-ASCII tile still makes.
+template <bool QUADS>
 __device__ __forceinline__ uint32_t word_error_after_carry(const Carry& c, uint32_t w) {
+  if constexpr (QUADS) {
+    // byte 3 of each carry word is the last byte before the tile
+    return word_error_after(c.p, c.f, prmt(c.ha, c.hb, 0x7300), lut_word(w));
+  }
   // the carry's stream-1 bytes 1 and 3 are the last two bytes before the tile
-  return word_error_after(prmt(c.x7, 0, 0x3144), prmt(c.f7, 0, 0x3144), prmt(c.h7, 0, 0x3144),
+  return word_error_after(prmt(c.p, 0, 0x3144), prmt(c.f, 0, 0x3144), prmt(c.hb, 0, 0x3144),
                           lut_word(w));
 }
 
@@ -162,20 +179,28 @@ __device__ __forceinline__ void interior_tiles(const Span& s, uint64_t& first, u
   last = (s.off + s.n) / tb;
 }
 
-// Checks one loaded tile.  Rows 2p and 2p+1 are processed together as two
-// interleaved streams (see lut_interleaved): e[p][m] is the error word of
-// interleaved word W_m = (row 2p byte 2m, row 2p+1 byte 2m, row 2p byte
-// 2m+1, row 2p+1 byte 2m+1) of this lane's granules.  `carry` describes the
-// bytes before the tile (lane 0) and is updated.
+// Checks one loaded tile.  e holds ROWS * 4 error words per lane, e[i / 8][i % 8]
+// for word i; a position is an error iff its byte is non-zero
+// (interleaved_position gives each byte's position).
+//  * QUADS (the default where ROWS is a multiple of 4): rows 4q .. 4q+3 are
+//    processed together as four streams, word i = 16q + k being W_k = (byte k
+//    of row 4q, of row 4q+1, of row 4q+2, of row 4q+3) of this lane's granules
+//    (see lut_quad): byte j's previous bytes are byte j of W_{k-1}, W_{k-2},
+//    W_{k-3}.
+//  * Row pairs: rows 2p and 2p+1 are processed as two interleaved streams,
+//    word i = 8p + m being W_m = (row 2p byte 2m, row 2p+1 byte 2m, row 2p
+//    byte 2m+1, row 2p+1 byte 2m+1) (see lut_interleaved); the previous bytes
+//    are a 16-bit funnel shift away.
+// `carry` describes the bytes before the tile (lane 0) and is updated.
 //
 // The all-ASCII test first votes on the tile's first row (512 bytes) alone:
 // on text with non-ASCII characters that row almost always holds one, and the
 // tile goes straight to the classification without OR-ing its other rows;
 // only a tile whose first row is ASCII pays for the full test.
-template <int ROWS>
+template <int ROWS, bool QUADS = kQuadRows<ROWS>>
 __device__ __forceinline__ void check_tile(const uint4 (&d)[ROWS], Carry& carry, int lane,
                                            uint32_t merge_sel, uint32_t (&e)[ROWS / 2][8]) {
-  static_assert(ROWS % 2 == 0, "rows are processed in pairs");
+  static_assert(QUADS ? ROWS % 4 == 0 : ROWS % 2 == 0, "whole row groups");
   const int left = (lane + kLanes - 1) & (kLanes - 1);
   const uint32_t sample = d[0].x | d[0].y | d[0].z | d[0].w;
   bool ascii = false;
@@ -193,57 +218,105 @@ __device__ __forceinline__ void check_tile(const uint4 (&d)[ROWS], Carry& carry,
 #pragma unroll
       for (int m = 0; m < 8; ++m) e[p][m] = 0;
     if (lane == 0) {
-      const uint32_t first = word_error_after_carry(carry, d[0].x);
-      e[0][0] = prmt(first, 0, 0x4140);  // positions 0, 1 of row 0
-      e[0][1] = prmt(first, 0, 0x4342);  // positions 2, 3 of row 0
+      const uint32_t first = word_error_after_carry<QUADS>(carry, d[0].x);
+      if constexpr (QUADS) {
+        // positions 0..3 of row 0: byte 0 of W_0 .. W_3
+        e[0][0] = first & 0xFFu;
+        e[0][1] = (first >> 8) & 0xFFu;
+        e[0][2] = (first >> 16) & 0xFFu;
+        e[0][3] = first >> 24;
+      } else {
+        e[0][0] = prmt(first, 0, 0x4140);  // positions 0, 1 of row 0
+        e[0][1] = prmt(first, 0, 0x4342);  // positions 2, 3 of row 0
+      }
     }
     carry = ascii_carry();
     return;
   }
+  if constexpr (QUADS) {
 #pragma unroll
-  for (int p = 0; p < ROWS / 2; ++p) {
-    const uint4 c = d[2 * p], n = d[2 * p + 1];
-    WordLut W[8];
-    lut_interleaved(c.x, n.x, W[0], W[1]);
-    lut_interleaved(c.y, n.y, W[2], W[3]);
-    lut_interleaved(c.z, n.z, W[4], W[5]);
-    lut_interleaved(c.w, n.w, W[6], W[7]);
-    // flags of each word's previous bytes (prev1) and back23 of each word
-    uint32_t g[8], h[8];
+    for (int q = 0; q < ROWS / 4; ++q) {
+      const uint4 a = d[4 * q], b = d[4 * q + 1], c = d[4 * q + 2], dd = d[4 * q + 3];
+      WordLut W[16];
+      lut_quad(a.x, b.x, c.x, dd.x, *reinterpret_cast<WordLut(*)[4]>(&W[0]));
+      lut_quad(a.y, b.y, c.y, dd.y, *reinterpret_cast<WordLut(*)[4]>(&W[4]));
+      lut_quad(a.z, b.z, c.z, dd.z, *reinterpret_cast<WordLut(*)[4]>(&W[8]));
+      lut_quad(a.w, b.w, c.w, dd.w, *reinterpret_cast<WordLut(*)[4]>(&W[12]));
+      uint32_t h[16];
 #pragma unroll
-    for (int m = 1; m < 8; ++m) {
-      g[m] = __funnelshift_l(W[m - 1].flags, W[m].flags, 16);
-      h[m] = back23(W[m].flags, g[m]);
+      for (int k = 1; k < 16; ++k) h[k] = back23(W[k].flags, W[k - 1].flags);
+      // left neighbour's W_15; lane 0 takes row 0 from the carry (the row
+      // before the quad) and rows 1..3 from rows 0..2 of lane 31
+      const uint32_t p15 = __shfl_sync(kFull, W[15].prev_side, left);
+      const uint32_t f15 = __shfl_sync(kFull, W[15].flags, left);
+      const uint32_t h14 = __shfl_sync(kFull, h[14], left);
+      const uint32_t h15 = __shfl_sync(kFull, h[15], left);
+      const uint32_t lp = prmt(carry.p, p15, merge_sel);
+      const uint32_t lf = prmt(carry.f, f15, merge_sel);
+      const uint32_t lh14 = prmt(carry.ha, h14, merge_sel);
+      const uint32_t lh15 = prmt(carry.hb, h15, merge_sel);
+      carry = Carry{p15, f15, h14, h15};
+      h[0] = back23(W[0].flags, lf);
+      uint32_t* eq = &e[2 * q][0];
+      eq[0] = position_errors(lp, W[0].cur_side, lf, lh14);
+      eq[1] = position_errors(W[0].prev_side, W[1].cur_side, W[0].flags, lh15);
+#pragma unroll
+      for (int k = 2; k < 16; ++k)
+        eq[k] = position_errors(W[k - 1].prev_side, W[k].cur_side, W[k - 1].flags, h[k - 2]);
     }
-    // left neighbour's W_7; lane 0 takes its first stream from the carry
-    // (the row before) and its second stream from lane 31 of the first row
-    const uint32_t x7 = __shfl_sync(kFull, W[7].prev_side, left);
-    const uint32_t f7 = __shfl_sync(kFull, W[7].flags, left);
-    const uint32_t h7 = __shfl_sync(kFull, h[7], left);
-    const uint32_t lx = prmt(carry.x7, x7, merge_sel);
-    const uint32_t lf = prmt(carry.f7, f7, merge_sel);
-    const uint32_t lh = prmt(carry.h7, h7, merge_sel);
-    carry = Carry{x7, f7, h7};
-    g[0] = __funnelshift_l(lf, W[0].flags, 16);
-    h[0] = back23(W[0].flags, g[0]);
-    e[p][0] = position_errors(__funnelshift_l(lx, W[0].prev_side, 16), W[0].cur_side, g[0], lh);
+  } else {
 #pragma unroll
-    for (int m = 1; m < 8; ++m)
-      e[p][m] = position_errors(__funnelshift_l(W[m - 1].prev_side, W[m].prev_side, 16),
-                                W[m].cur_side, g[m], h[m - 1]);
+    for (int p = 0; p < ROWS / 2; ++p) {
+      const uint4 c = d[2 * p], n = d[2 * p + 1];
+      WordLut W[8];
+      lut_interleaved(c.x, n.x, W[0], W[1]);
+      lut_interleaved(c.y, n.y, W[2], W[3]);
+      lut_interleaved(c.z, n.z, W[4], W[5]);
+      lut_interleaved(c.w, n.w, W[6], W[7]);
+      // flags of each word's previous bytes (prev1) and back23 of each word
+      uint32_t g[8], h[8];
+#pragma unroll
+      for (int m = 1; m < 8; ++m) {
+        g[m] = __funnelshift_l(W[m - 1].flags, W[m].flags, 16);
+        h[m] = back23(W[m].flags, g[m]);
+      }
+      // left neighbour's W_7; lane 0 takes its first stream from the carry
+      // (the row before) and its second stream from lane 31 of the first row
+      const uint32_t x7 = __shfl_sync(kFull, W[7].prev_side, left);
+      const uint32_t f7 = __shfl_sync(kFull, W[7].flags, left);
+      const uint32_t h7 = __shfl_sync(kFull, h[7], left);
+      const uint32_t lx = prmt(carry.p, x7, merge_sel);
+      const uint32_t lf = prmt(carry.f, f7, merge_sel);
+      const uint32_t lh = prmt(carry.hb, h7, merge_sel);
+      carry = Carry{x7, f7, 0u, h7};
+      g[0] = __funnelshift_l(lf, W[0].flags, 16);
+      h[0] = back23(W[0].flags, g[0]);
+      e[p][0] = position_errors(__funnelshift_l(lx, W[0].prev_side, 16), W[0].cur_side, g[0], lh);
+#pragma unroll
+      for (int m = 1; m < 8; ++m)
+        e[p][m] = position_errors(__funnelshift_l(W[m - 1].prev_side, W[m].prev_side, 16),
+                                  W[m].cur_side, g[m], h[m - 1]);
+    }
   }
 }
 
-// Virtual position (relative to the tile start) of byte b of interleaved
-// error word m of row pair p in lane `lane`.
-template <int ROWS>
+// Virtual position (relative to the tile start) of byte b of error word
+// e[p][m] in lane `lane` (see check_tile).
+template <int ROWS, bool QUADS = kQuadRows<ROWS>>
 __device__ __forceinline__ uint32_t interleaved_position(int p, int m, int b, int lane) {
+  if constexpr (QUADS) {
+    const int i = p * 8 + m;
+    const int row = 4 * (i >> 4) + b;
+    return (uint32_t)(row * kLanes + lane) * 16u + (uint32_t)(i & 15);
+  }
   const int row = 2 * p + (b & 1);
   return (uint32_t)(row * kLanes + lane) * 16u + (uint32_t)(2 * m + (b >> 1));
 }
 
 // Selector merging the carry into lane 0's left neighbour (see check_tile).
+template <bool QUADS>
 __device__ __forceinline__ uint32_t carry_merge_selector(int lane) {
+  if constexpr (QUADS) return lane == 0 ? 0x6543u : 0x7654u;
   return lane == 0 ? 0x6341u : 0x7654u;
 }
 
@@ -307,15 +380,15 @@ constexpr uint32_t kPollBytes = 16 << 10;
 // of the run are [i0, i0 + i_len).  The run is set up here as in run_tiles,
 // written out: through run_tiles and load_run_tile this loop compiled 0.8%
 // slower.
-template <int ROWS>
+template <int ROWS, bool QUADS = kQuadRows<ROWS>>
 __device__ __forceinline__ uint32_t warp_check_tiles(const Span& s, uint64_t t_begin,
                                                      uint64_t t_end) {
   constexpr uint64_t tb = TileGeom<ROWS>::kBytes;
   const int lane = threadIdx.x & (kLanes - 1);
   uint32_t err = 0;
-  const uint32_t merge_sel = carry_merge_selector(lane);
+  const uint32_t merge_sel = carry_merge_selector<QUADS>(lane);
   Carry carry = ascii_carry();  // zeros before the stream
-  if (t_begin < t_end && t_begin > 0) carry = halo_carry(load_word(s, t_begin * tb - 4));
+  if (t_begin < t_end && t_begin > 0) carry = halo_carry<QUADS>(load_word(s, t_begin * tb - 4));
   uint64_t in0, in1;
   interior_tiles<ROWS>(s, in0, in1);
   const uint8_t* lane_ptr = s.abase + t_begin * tb + lane * 16;
@@ -337,7 +410,7 @@ __device__ __forceinline__ uint32_t warp_check_tiles(const Span& s, uint64_t t_b
     for (int r = 0; r < ROWS; ++r) d[r] = next[r];
     if (k + 1 < cnt) load_rel(k + 1, lane_ptr + tb, next);
     uint32_t e[ROWS / 2][8];
-    check_tile<ROWS>(d, carry, lane, merge_sel, e);
+    check_tile<ROWS, QUADS>(d, carry, lane, merge_sel, e);
 #pragma unroll
     for (int p = 0; p < ROWS / 2; ++p)
 #pragma unroll
@@ -353,7 +426,7 @@ __device__ __forceinline__ uint32_t warp_check_tiles(const Span& s, uint64_t t_b
 // shows an error; errors in the tiles it skips cannot change the answer.
 // The split loop costs about 2% of the classification rate on valid text
 // (the single loop above schedules better), so polling is the caller's choice.
-template <int ROWS>
+template <int ROWS, bool QUADS = kQuadRows<ROWS>>
 __device__ __forceinline__ uint32_t warp_check_tiles_polling(const Span& s, uint64_t t_begin,
                                                              uint64_t t_end,
                                                              const uint8_t* result) {
@@ -362,9 +435,9 @@ __device__ __forceinline__ uint32_t warp_check_tiles_polling(const Span& s, uint
   static_assert(poll_tiles >= 1, "a poll falls after whole tiles");
   const int lane = threadIdx.x & (kLanes - 1);
   uint32_t err = 0;
-  const uint32_t merge_sel = carry_merge_selector(lane);
+  const uint32_t merge_sel = carry_merge_selector<QUADS>(lane);
   Carry carry = ascii_carry();  // zeros before the stream
-  if (t_begin < t_end && t_begin > 0) carry = halo_carry(load_word(s, t_begin * tb - 4));
+  if (t_begin < t_end && t_begin > 0) carry = halo_carry<QUADS>(load_word(s, t_begin * tb - 4));
   const RunTiles run = run_tiles<ROWS>(s, t_begin, t_end);
   const uint8_t* lane_ptr = s.abase + t_begin * tb + lane * 16;
   const bool poll = poll_tiles < run.cnt;
@@ -381,7 +454,7 @@ __device__ __forceinline__ uint32_t warp_check_tiles_polling(const Span& s, uint
       if (k + 1 < run.cnt)
         load_run_tile<ROWS>(s, run, t_begin, k + 1, lane, lane_ptr + tb, next);
       uint32_t e[ROWS / 2][8];
-      check_tile<ROWS>(d, carry, lane, merge_sel, e);
+      check_tile<ROWS, QUADS>(d, carry, lane, merge_sel, e);
 #pragma unroll
       for (int p = 0; p < ROWS / 2; ++p)
 #pragma unroll

@@ -21,8 +21,10 @@
 namespace utf8gpu {
 
 // Tiles [t_first, t_first + tiles) are split into one contiguous run per warp.
+// Two CTAs per SM: the row-quad classification fits 128 registers with a few
+// bytes spilled (without the bound it takes 141, one CTA per SM).
 template <int ROWS, bool POLL>
-__global__ void __launch_bounds__(kBlockThreads) validate_kernel(Span s, uint64_t t_first,
+__global__ void __launch_bounds__(kBlockThreads, 2) validate_kernel(Span s, uint64_t t_first,
                                                                 uint64_t tiles,
                                                                 uint8_t* out_valid) {
   const uint64_t warps = (uint64_t)gridDim.x * (kBlockThreads / kLanes);

@@ -84,3 +84,77 @@ def test_every_class_string_up_to_6_bytes():
             offsets = np.arange(0, s.size + 1, n, dtype=np.int64)
             want = oracle.valid_batch(s.reshape(-1), offsets, threads=4) == 1
             assert np.array_equal(model_valid(s), want), n
+
+
+# ---------------------------------------------------------------------------
+# The byte-permute lookups of the row-quad layout (lut_quad in
+# csrc/lookup.cuh), restated with a model of PTX `prmt` (default mode): for
+# result byte i, selector nibble i picks byte (nibble & 7) of the eight bytes
+# {b, a}; with nibble bit 3 set the result is that byte's sign bit replicated.
+# ---------------------------------------------------------------------------
+def prmt(a, b, sel):
+    a, b, sel = np.broadcast_arrays(np.asarray(a, np.uint64), np.asarray(b, np.uint64),
+                                    np.asarray(sel, np.uint64))
+    pool = np.stack([(a >> np.uint64(8 * k)) & np.uint64(0xFF) for k in range(4)] +
+                    [(b >> np.uint64(8 * k)) & np.uint64(0xFF) for k in range(4)])
+    out = np.zeros(a.shape, np.uint64)
+    cols = np.arange(a.size)
+    for i in range(4):
+        nib = (sel >> np.uint64(4 * i)) & np.uint64(0xF)
+        v = pool[(nib & np.uint64(7)).astype(np.int64).ravel(), cols].reshape(a.shape)
+        sign = np.where(v & np.uint64(0x80), np.uint64(0xFF), np.uint64(0))
+        v = np.where(nib & np.uint64(8), sign, v)
+        out |= v << np.uint64(8 * i)
+    return out
+
+
+def pack4(t):
+    return sum(int(t[k]) << (8 * k) for k in range(4))
+
+
+def halves(table, reversed_):
+    """The two words of an 8-entry prmt table: entries 0..7 (plain selector)
+    or 15..8 (complemented selector)."""
+    e = table[::-1] if reversed_ else table
+    return pack4(e[0:4]), pack4(e[4:8])
+
+
+def lut_quad(a, b, c, d):
+    """Per j = 0..3: (prev_side, cur_side, flags) of W_j = (a_j, b_j, c_j, d_j)."""
+    m = np.uint64(0x0F0F0F0F)
+    full = np.uint64(0xFFFFFFFF)
+    sel_not = lambda x, y: ~((x & m) | (y & ~m)) & full
+    sel = lambda x, y: ((x & m) | (y & ~m)) & full
+    hab = sel_not(a >> np.uint64(4), b)
+    hcd = sel_not(c >> np.uint64(4), d)
+    lab = sel(a, (b << np.uint64(4)) & full)
+    lcd = sel(c, (d << np.uint64(4)) & full)
+    b1h, b2h, flg = halves(BYTE1_HIGH, True), halves(BYTE2_HIGH, True), halves(LEAD_FLAGS, True)
+    b1l_plain, b1l_rev = halves(BYTE1_LOW, False), halves(BYTE1_LOW, True)
+    words = []
+    for j in range(4):
+        s = np.uint64(j | ((4 + j) << 4))
+        hi_c = prmt(hab, hcd, s)
+        lo = prmt(lab, lcd, s)
+        lo_c = ~lo & full
+        prev = prmt(*b1h, hi_c) & prmt(*b1l_plain, lo) & prmt(*b1l_rev, lo_c)
+        words.append((prev, prmt(*b2h, hi_c), prmt(*flg, hi_c)))
+    return words
+
+
+def test_quad_lookups_are_the_tables():
+    """Byte r of W_j's lookups is the tables' value for byte j of row r, for
+    random words and for every byte value in every byte slot."""
+    rng = np.random.default_rng(3)
+    rows = rng.integers(0, 1 << 32, (4, 4096), dtype=np.uint64)
+    every = np.arange(256, dtype=np.uint64)
+    for r in range(4):  # byte value v in byte slot j of row r (j = v % 4)
+        rows[r, :256] = every << np.uint64(8 * (int(r) % 4))
+    words = lut_quad(*rows)
+    for j in range(4):
+        for r in range(4):
+            byte = ((rows[r] >> np.uint64(8 * j)) & np.uint64(0xFF)).astype(np.int64)
+            got = [((w >> np.uint64(8 * r)) & np.uint64(0xFF)).astype(np.int64) for w in words[j]]
+            assert np.array_equal(got[0], BYTE1_HIGH[byte >> 4] & BYTE1_LOW[byte & 15])
+            assert np.array_equal(got[1], BYTE2_HIGH[byte >> 4])
+            assert np.array_equal(got[2], LEAD_FLAGS[byte >> 4])
