@@ -390,7 +390,11 @@ int utf8_tune_cache_save(const char* path);
 
 /*
  * Writes the launch configuration in use on the current device as a short
- * JSON object into buf (at most cap bytes, NUL terminated).  Returns the
+ * JSON object into buf (at most cap bytes, NUL terminated): tile rows and
+ * CTAs per SM of the single-buffer and batch kernels, the SM count, whether
+ * early exit is on, and "staged": whether the 8-row single- and multi-buffer
+ * passes stage their tiles through shared memory (the default where the
+ * device allows it; UTF8GPU_STAGED=0 keeps them in registers).  Returns the
  * length it needed, or -1.
  */
 int utf8_config_json(char* buf, size_t cap);

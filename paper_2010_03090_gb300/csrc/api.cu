@@ -465,9 +465,10 @@ int utf8_config_json(char* buf, size_t cap) {
   const LaunchCfg cfg = config_of(*d);
   const int n = snprintf(tmp, sizeof tmp,
                          "{\"rows\": %d, \"blocks_per_sm\": %d, \"batch_rows\": %d, "
-                         "\"batch_blocks_per_sm\": %d, \"sm_count\": %d, \"early_exit\": %d}",
+                         "\"batch_blocks_per_sm\": %d, \"sm_count\": %d, \"early_exit\": %d, "
+                         "\"staged\": %d}",
                          cfg.rows, cfg.blocks_per_sm, cfg.batch_rows, cfg.batch_blocks_per_sm,
-                         d->sm_count, early_exit_enabled() ? 1 : 0);
+                         d->sm_count, early_exit_enabled() ? 1 : 0, cfg.staged ? 1 : 0);
   if (buf != nullptr && cap > 0) {
     strncpy(buf, tmp, cap - 1);
     buf[cap - 1] = 0;

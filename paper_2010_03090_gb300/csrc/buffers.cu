@@ -35,7 +35,9 @@ struct BuffersArgs {
   uint32_t chunk_tiles;
 };
 
-template <int ROWS>
+// STAGED: tiles through shared memory (the launch's dynamic shared memory
+// holds each warp's ring, see warp_check_tiles_staged).
+template <int ROWS, bool STAGED>
 __global__ void __launch_bounds__(kBlockThreads, 2) buffers_kernel(BuffersArgs a, unsigned* next,
                                                                uint8_t* out_valid) {
   const int lane = threadIdx.x & (kLanes - 1);
@@ -56,7 +58,14 @@ __global__ void __launch_bounds__(kBlockThreads, 2) buffers_kernel(BuffersArgs a
     const uint64_t all = span_tiles<ROWS>(a.s[b]);
     const uint64_t t0 = round * a.chunk_tiles;
     const uint64_t t1 = t0 + a.chunk_tiles < all ? t0 + a.chunk_tiles : all;
-    const uint32_t err = warp_check_tiles<ROWS>(a.s[b], t0, t1);
+    uint32_t err;
+    if constexpr (STAGED) {
+      extern __shared__ uint4 buffers_rings[];
+      err = warp_check_tiles_staged<ROWS>(
+          a.s[b], t0, t1, buffers_rings + (threadIdx.x / kLanes) * kStages * ROWS * kLanes);
+    } else {
+      err = warp_check_tiles<ROWS>(a.s[b], t0, t1);
+    }
     if (__any_sync(kFull, err != 0) && lane == 0) clear_result(out_valid + b);
     c = __shfl_sync(kFull, c_next, 0);
   }
@@ -64,8 +73,16 @@ __global__ void __launch_bounds__(kBlockThreads, 2) buffers_kernel(BuffersArgs a
 
 template <int ROWS>
 cudaError_t launch_rows(const BuffersArgs& a, unsigned* next, uint8_t* out_valid, int blocks,
-                        cudaStream_t st) {
-  buffers_kernel<ROWS><<<(unsigned)blocks, kBlockThreads, 0, st>>>(a, next, out_valid);
+                        bool staged, cudaStream_t st) {
+  if constexpr (ROWS == 8) {
+    if (staged) {
+      buffers_kernel<ROWS, true>
+          <<<(unsigned)blocks, kBlockThreads, staged_smem_bytes<ROWS>(kBlockThreads), st>>>(
+              a, next, out_valid);
+      return cudaGetLastError();
+    }
+  }
+  buffers_kernel<ROWS, false><<<(unsigned)blocks, kBlockThreads, 0, st>>>(a, next, out_valid);
   return cudaGetLastError();
 }
 
@@ -114,10 +131,20 @@ cudaError_t launch_buffers(const uint8_t* const* data, const size_t* lens, int c
   if (e != cudaSuccess) return e;
   const int blocks = sm_count * cfg.blocks_per_sm;
   switch (rows) {
-    case 2: return launch_rows<2>(a, next, out_valid, blocks, st);
-    case 8: return launch_rows<8>(a, next, out_valid, blocks, st);
-    default: return launch_rows<4>(a, next, out_valid, blocks, st);
+    case 2: return launch_rows<2>(a, next, out_valid, blocks, false, st);
+    case 8: return launch_rows<8>(a, next, out_valid, blocks, cfg.staged, st);
+    default: return launch_rows<4>(a, next, out_valid, blocks, false, st);
   }
+}
+
+cudaError_t prepare_buffers_staged() {
+  const int smem = staged_smem_bytes<8>(kBlockThreads);
+  cudaError_t e = cudaFuncSetAttribute(buffers_kernel<8, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(buffers_kernel<8, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  return e;
 }
 
 }  // namespace utf8gpu

@@ -19,7 +19,19 @@ struct LaunchCfg {
   int blocks_per_sm = 8;  // resident CTAs per SM in the persistent grid
   int batch_rows = 8;     // tile rows for the batch kernel: 2, 4 or 8
   int batch_blocks_per_sm = 8;
+  // 8-row single- and multi-buffer passes stage their tiles through shared
+  // memory (tiles.cuh, warp_check_tiles_staged); set by clamp_to_occupancy
+  // once this device's kernels accept the shared memory, never read from a
+  // tuning cache
+  bool staged = false;
 };
+
+// Lets the staged kernels use their shared memory on the current device
+// (validate.cu, buffers.cu); clamp_to_occupancy calls it.
+cudaError_t prepare_staged_kernels();
+cudaError_t prepare_buffers_staged();
+// Resident CTAs per SM of the staged single-buffer kernel (0 if it cannot run).
+int staged_blocks_per_sm();
 
 cudaError_t launch_validate(const uint8_t* data, uint64_t n, uint8_t* out_valid,
                             const LaunchCfg& cfg, int sm_count, cudaStream_t st);

@@ -468,4 +468,91 @@ __device__ __forceinline__ uint32_t warp_check_tiles_polling(const Span& s, uint
   return err;
 }
 
+// ---------------------------------------------------------------------------
+// Staged form of warp_check_tiles: the coming tiles are copied into shared
+// memory with cp.async, kStages - 1 tiles ahead of the one being classified,
+// so no register holds a tile in flight (the register form keeps the next
+// tile in 32 registers, one tile ahead).  The deeper lead and the freed
+// registers measured 4% faster on non-ASCII text at 8 rows.
+//
+// `ring` is this warp's kStages slots of ROWS * 32 granules in shared memory.
+// Each lane copies, and later reads back, only its own granules of a slot,
+// so the lanes need no barrier: cp.async.wait_group makes a lane wait for its
+// own copies.  A slot is refilled only after the lane has classified the tile
+// it held (every loaded word feeds the classification before the refill is
+// issued).  The first and last tiles of a stream take the checked loads and
+// are stored to the slot directly.
+// ---------------------------------------------------------------------------
+constexpr int kStages = 3;
+
+// Shared memory of the rings of one CTA of `threads` threads.
+template <int ROWS>
+constexpr int staged_smem_bytes(int threads) {
+  return (threads / kLanes) * kStages * ROWS * kLanes * 16;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int ROWS, bool QUADS = kQuadRows<ROWS>>
+__device__ __forceinline__ uint32_t warp_check_tiles_staged(const Span& s, uint64_t t_begin,
+                                                            uint64_t t_end, uint4* ring) {
+  constexpr uint64_t tb = TileGeom<ROWS>::kBytes;
+  constexpr int kSlot = ROWS * kLanes;  // granules per slot
+  const int lane = threadIdx.x & (kLanes - 1);
+  uint32_t err = 0;
+  const uint32_t merge_sel = carry_merge_selector<QUADS>(lane);
+  Carry carry = ascii_carry();  // zeros before the stream
+  if (t_begin < t_end && t_begin > 0) carry = halo_carry<QUADS>(load_word(s, t_begin * tb - 4));
+  const RunTiles run = run_tiles<ROWS>(s, t_begin, t_end);
+  const uint8_t* lane_ptr = s.abase + t_begin * tb + lane * 16;
+  // tile t_begin + k into a slot: cp.async when interior, checked loads else
+  const auto issue = [&](uint32_t k, uint4* slot) {
+    if (k - run.i0 < run.i_len) {
+      const uint8_t* p = lane_ptr + (uint64_t)k * tb;
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) cp_async16(&slot[r * kLanes + lane], p + r * kLanes * 16);
+    } else {
+      const uint64_t g0 = (t_begin + k) * TileGeom<ROWS>::kGranules;
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r)
+        slot[r * kLanes + lane] = load_granule(s, g0 + r * kLanes + lane);
+    }
+  };
+#pragma unroll
+  for (int j = 0; j < kStages - 1; ++j) {
+    if ((uint32_t)j < run.cnt) issue((uint32_t)j, ring + j * kSlot);
+    cp_async_commit();
+  }
+  int rd = 0, wr = kStages - 1;
+  for (uint32_t k = 0; k < run.cnt; ++k) {
+    if (k + kStages - 1 < run.cnt) issue(k + kStages - 1, ring + wr * kSlot);
+    cp_async_commit();  // one group per iteration, empty or not
+    cp_async_wait<kStages - 1>();  // tile k's group is complete
+    const uint4* slot = ring + rd * kSlot;
+    uint4 d[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) d[r] = slot[r * kLanes + lane];
+    rd = rd + 1 == kStages ? 0 : rd + 1;
+    wr = wr + 1 == kStages ? 0 : wr + 1;
+    uint32_t e[ROWS / 2][8];
+    check_tile<ROWS, QUADS>(d, carry, lane, merge_sel, e);
+#pragma unroll
+    for (int p = 0; p < ROWS / 2; ++p)
+#pragma unroll
+      for (int m = 0; m < 8; ++m) err |= e[p][m];
+  }
+  cp_async_wait<0>();
+  return err;
+}
+
 }  // namespace utf8gpu

@@ -109,6 +109,15 @@ LaunchCfg tuned_config(const char* gpu_name, int sm_count) {
   return c;
 }
 
+// The staged 8-row passes run where this device's kernels accept their shared
+// memory and the grid's CTAs per SM fit beside it; else the register form.
+// UTF8GPU_STAGED=0 keeps the register form.
+static void apply_staged(LaunchCfg& cfg) {
+  cfg.staged = cfg.rows == 8 && env_int("UTF8GPU_STAGED", 1) != 0 &&
+               prepare_staged_kernels() == cudaSuccess &&
+               cfg.blocks_per_sm <= staged_blocks_per_sm();
+}
+
 void clamp_to_occupancy(LaunchCfg& cfg) {
   if (cfg.rows != 2 && cfg.rows != 4 && cfg.rows != 8) cfg.rows = 8;
   if (cfg.batch_rows != 2 && cfg.batch_rows != 4 && cfg.batch_rows != 8) cfg.batch_rows = 8;
@@ -116,6 +125,7 @@ void clamp_to_occupancy(LaunchCfg& cfg) {
   const int b = batch_blocks_per_sm(cfg.batch_rows);
   if (cfg.blocks_per_sm < 1 || cfg.blocks_per_sm > v) cfg.blocks_per_sm = v;
   if (cfg.batch_blocks_per_sm < 1 || cfg.batch_blocks_per_sm > b) cfg.batch_blocks_per_sm = b;
+  apply_staged(cfg);
 }
 
 static float time_ms(cudaStream_t st, cudaEvent_t a, cudaEvent_t b, int reps,
@@ -188,6 +198,7 @@ int run_autotune(int flags) {
         c.rows = rows_c[r];
         c.blocks_per_sm = bps_c[k];
         if (c.blocks_per_sm > validate_blocks_per_sm(c.rows)) continue;
+        apply_staged(c);
         const float ms = time_ms(st, a, b, 10, c, sms, false, data, bytes, offsets, count, out);
         if (ms < best_single) { best_single = ms; best.rows = c.rows; best.blocks_per_sm = c.blocks_per_sm; }
       }

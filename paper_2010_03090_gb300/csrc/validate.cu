@@ -21,9 +21,11 @@
 namespace utf8gpu {
 
 // Tiles [t_first, t_first + tiles) are split into one contiguous run per warp.
-// Two CTAs per SM: the row-quad classification fits 128 registers with a few
-// bytes spilled (without the bound it takes 141, one CTA per SM).
-template <int ROWS, bool POLL>
+// Two CTAs per SM: the register form of the row-quad classification fits 128
+// registers with a few bytes spilled (without the bound it takes 141, one CTA
+// per SM); the staged form (STAGED: tiles through shared memory, the
+// launch's dynamic shared memory holding each warp's ring) takes 115.
+template <int ROWS, bool POLL, bool STAGED = false>
 __global__ void __launch_bounds__(kBlockThreads, 2) validate_kernel(Span s, uint64_t t_first,
                                                                 uint64_t tiles,
                                                                 uint8_t* out_valid) {
@@ -32,8 +34,16 @@ __global__ void __launch_bounds__(kBlockThreads, 2) validate_kernel(Span s, uint
   const uint64_t t0 = t_first + tiles * w / warps;
   const uint64_t t1 = t_first + tiles * (w + 1) / warps;
   uint32_t err;
-  if constexpr (POLL) err = warp_check_tiles_polling<ROWS>(s, t0, t1, out_valid);
-  else err = warp_check_tiles<ROWS>(s, t0, t1);
+  if constexpr (STAGED) {
+    static_assert(!POLL, "the staged form has no early exit");
+    extern __shared__ uint4 validate_rings[];
+    err = warp_check_tiles_staged<ROWS>(
+        s, t0, t1, validate_rings + (threadIdx.x / kLanes) * kStages * ROWS * kLanes);
+  } else if constexpr (POLL) {
+    err = warp_check_tiles_polling<ROWS>(s, t0, t1, out_valid);
+  } else {
+    err = warp_check_tiles<ROWS>(s, t0, t1);
+  }
   if (__any_sync(kFull, err != 0) && (threadIdx.x & (kLanes - 1)) == 0) clear_result(out_valid);
 }
 
@@ -72,10 +82,19 @@ static cudaError_t launch_rows(const Span& s, uint64_t t_begin, uint64_t t_end,
   const uint64_t need = (tiles + warps_per_block - 1) / warps_per_block;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  if (early_exit_enabled())
+  if (early_exit_enabled()) {
     validate_kernel<ROWS, true><<<(unsigned)grid, kBlockThreads, 0, st>>>(s, t_begin, tiles, out_valid);
-  else
-    validate_kernel<ROWS, false><<<(unsigned)grid, kBlockThreads, 0, st>>>(s, t_begin, tiles, out_valid);
+    return cudaGetLastError();
+  }
+  if constexpr (ROWS == 8) {
+    if (cfg.staged) {
+      validate_kernel<ROWS, false, true>
+          <<<(unsigned)grid, kBlockThreads, staged_smem_bytes<ROWS>(kBlockThreads), st>>>(
+              s, t_begin, tiles, out_valid);
+      return cudaGetLastError();
+    }
+  }
+  validate_kernel<ROWS, false><<<(unsigned)grid, kBlockThreads, 0, st>>>(s, t_begin, tiles, out_valid);
   return cudaGetLastError();
 }
 
@@ -174,7 +193,33 @@ cudaError_t preload_validate_kernels() {
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, validate_kernel<4, true>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, validate_kernel<8, false>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, validate_kernel<8, true>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, validate_kernel<8, false, true>);
   return e;
+}
+
+cudaError_t prepare_staged_kernels() {
+  const int smem = staged_smem_bytes<8>(kBlockThreads);
+  cudaError_t e = cudaFuncSetAttribute(validate_kernel<8, false, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(validate_kernel<8, false, true>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess) e = prepare_buffers_staged();
+  if (e != cudaSuccess) cudaGetLastError();
+  return e;
+}
+
+int staged_blocks_per_sm() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, validate_kernel<8, false, true>,
+                                                    kBlockThreads,
+                                                    staged_smem_bytes<8>(kBlockThreads)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 int validate_blocks_per_sm(int rows) {
