@@ -97,11 +97,23 @@ __device__ void warp_lower_bound2(const int64_t* offsets, int64_t hi, int64_t ta
   res_b = lb_final(lo_b, hi_b, mask_b);
 }
 
-// The batch pass classifies its tiles as row pairs, not quads (tiles.cuh):
-// with quads its staging, boundary and charging state needs 169 registers, so
-// one CTA fits an SM, and the 1M-string batch ran 2.6% slower (1.4% slower
-// with quads at 4-row tiles, which fit two CTAs).
-constexpr bool kBatchQuads = false;
+// The batch pass classifies row quads where the tile height allows
+// (tiles.cuh).  Its tiles come through a ring of kStages slots per warp in
+// shared memory, filled by cp.async two tiles ahead: no register holds a tile
+// in flight, which leaves room for the quads' state beside the boundary and
+// charging state (with register loads quads took 169 registers, one CTA per
+// SM, and ran 2.6% slower than row pairs).
+template <int ROWS>
+constexpr bool kBatchQuads = kQuadRows<ROWS>;
+// A slot: the 8 bytes before its tile (header bytes 8..15), then the tile,
+// in 32-bit words.
+template <int ROWS>
+constexpr int kBatchSlotWords = 4 + ROWS * 32 * 4;
+// Dynamic shared memory of one CTA's rings.
+template <int ROWS>
+constexpr int batch_smem_bytes() {
+  return (kBlockThreads / 32) * kStages * kBatchSlotWords<ROWS> * 4;
+}
 
 // An error at `rel` bytes into string j: its flag is cleared, or (LOCATE) its
 // first erroneous position is lowered to rel (see locate.cuh).
@@ -134,6 +146,44 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
   const uint64_t t1 = tiles * (w + 1) / warps;
   if (t0 >= t1) return;
 
+  // Per warp: the 8 bytes before the current tile (bytes 8..15), then the
+  // tile itself (from byte 16), staged so that boundary windows are taken
+  // from it instead of being read again from memory.  A tile with errors
+  // reuses the tile part for its error words once its windows are taken.
+  constexpr int kSlotWords = kBatchSlotWords<ROWS>;
+  extern __shared__ __align__(16) uint32_t batch_rings[];
+  uint32_t* const ring = batch_rings + (threadIdx.x / kLanes) * kStages * kSlotWords;
+  uint32_t* stage = ring;
+  uint32_t* err_words = stage + 4;
+  // Tiles are counted from t0 in 32 bits (a warp's run is far below 2^32
+  // tiles); [r_in0, r_in1) are its tiles wholly inside the region.
+  const uint32_t n_tiles = (uint32_t)(t1 - t0);
+  uint64_t in0, in1;
+  interior_tiles<ROWS>(region, in0, in1);
+  const uint32_t r_in0 = (uint32_t)(in0 <= t0 ? 0 : (in0 - t0 < n_tiles ? in0 - t0 : n_tiles));
+  const uint32_t r_in1 = (uint32_t)(in1 <= t0 ? 0 : (in1 - t0 < n_tiles ? in1 - t0 : n_tiles));
+  const uint8_t* lane_ptr = region.abase + t0 * kTileBytes + lane * 16;
+  // the first tiles' copies go out before the boundary search
+  // tile t0 + k into its slot (data after the 16-byte header): cp.async when
+  // the tile lies inside the region, checked loads stored directly else
+  const auto issue = [&](uint32_t k) {
+    uint4* slot = reinterpret_cast<uint4*>(ring + (k % kStages) * kSlotWords + 4);
+    if (k >= r_in0 && k < r_in1) {
+      const uint8_t* p = lane_ptr + (uint64_t)k * kTileBytes;
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) cp_async16(&slot[r * kLanes + lane], p + r * kLanes * 16);
+    } else {
+      uint4 c[ROWS];
+      load_tile_checked<ROWS>(region, t0 + k, lane, c);
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) slot[r * kLanes + lane] = c[r];
+    }
+  };
+  issue(0);
+  cp_async_commit();
+  if (n_tiles > 1) issue(1);
+  cp_async_commit();
+  int rd = 0;
   // absolute offset of virtual position 0 of the region
   const int64_t vbase = o_first - (int64_t)region.off;
   const int64_t range_lo = vbase + (int64_t)(t0 * kTileBytes);
@@ -144,31 +194,16 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
   // strings that can hold a position of this warp: b0 - 1 .. b1 - 1
   const int64_t own_hi = b1 < count ? b1 : count;
 
-  // Per warp: the 8 bytes before the current tile (bytes 8..15), then the
-  // tile itself (from byte 16), staged so that boundary windows are taken
-  // from it instead of being read again from memory.  A tile with errors
-  // reuses the tile part for its error words once its windows are taken.
-  __shared__ __align__(16) uint32_t stage_smem[kBlockThreads / kLanes][4 + ROWS * kLanes * 4];
-  uint32_t* stage = stage_smem[threadIdx.x / kLanes];
-  uint32_t* err_words = stage + 4;
   static_assert(ROWS / 2 * 8 * kLanes == ROWS * kLanes * 4, "error words fit the tile part");
 
-  const uint32_t merge_sel = carry_merge_selector<kBatchQuads>(lane);
+  const uint32_t merge_sel = carry_merge_selector<kBatchQuads<ROWS>>(lane);
   Carry carry = ascii_carry();
   const uint32_t halo = t0 > 0 ? load_word(region, t0 * kTileBytes - 4) : 0u;
-  if (t0 > 0) carry = halo_carry<kBatchQuads>(halo);
+  if (t0 > 0) carry = halo_carry<kBatchQuads<ROWS>>(halo);
   if (lane == 0) {
     stage[2] = t0 > 0 ? load_word(region, t0 * kTileBytes - 8) : 0u;
     stage[3] = halo;
   }
-  // Tiles are counted from t0 in 32 bits (a warp's run is far below 2^32
-  // tiles); [r_in0, r_in1) are its tiles wholly inside the region.
-  const uint32_t n_tiles = (uint32_t)(t1 - t0);
-  uint64_t in0, in1;
-  interior_tiles<ROWS>(region, in0, in1);
-  const uint32_t r_in0 = (uint32_t)(in0 <= t0 ? 0 : (in0 - t0 < n_tiles ? in0 - t0 : n_tiles));
-  const uint32_t r_in1 = (uint32_t)(in1 <= t0 ? 0 : (in1 - t0 < n_tiles ? in1 - t0 : n_tiles));
-  const uint8_t* lane_ptr = region.abase + t0 * kTileBytes + lane * 16;
 
   // Boundary groups of up to 32, [next_group, group_last]; lane k holds
   // g_off = offsets[next_group + k] (INT64_MAX past the group) and every lane
@@ -224,27 +259,23 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
     }
   };
 
-  uint4 next[ROWS];  // the next tile's loads, issued one tile ahead
-  if (r_in0 == 0 && r_in1 > 0) load_tile_interior<ROWS>(lane_ptr, next);
-  else load_tile_checked<ROWS>(region, t0, lane, next);
 
-  for (uint32_t i = 0; i < n_tiles; ++i, lane_ptr += kTileBytes) {
+  for (uint32_t i = 0; i < n_tiles; ++i) {
     // ---- stream the tile (plain `lookup` over the concatenation) ----------
+    if (i + 2 < n_tiles) issue(i + 2);
+    cp_async_commit();
+    cp_async_wait<kStages - 1>();
+    __syncwarp();  // every lane's part of tile i is in its slot
+    stage = ring + rd * kSlotWords;
+    err_words = stage + 4;
     uint4 d[ROWS];
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) d[r] = next[r];
-    if (i + 1 < n_tiles) {
-      if (i + 1 >= r_in0 && i + 1 < r_in1) load_tile_interior<ROWS>(lane_ptr + kTileBytes, next);
-      else load_tile_checked<ROWS>(region, t0 + i + 1, lane, next);
-    }
+    for (int r = 0; r < ROWS; ++r) d[r] = reinterpret_cast<const uint4*>(stage + 4)[r * kLanes + lane];
     const int64_t tile_lo = vbase + (int64_t)((t0 + i) * kTileBytes);
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r) reinterpret_cast<uint4*>(stage + 4)[r * kLanes + lane] = d[r];
-    __syncwarp();
     take_windows(tile_lo, true);
     bool staged = true;  // the stage still holds this tile
     uint32_t e[ROWS / 2][8];
-    check_tile<ROWS, kBatchQuads>(d, carry, lane, merge_sel, e);
+    check_tile<ROWS, kBatchQuads<ROWS>>(d, carry, lane, merge_sel, e);
     uint32_t any_err = 0;
 #pragma unroll
     for (int p = 0; p < ROWS / 2; ++p)
@@ -272,25 +303,31 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
         }
       __syncwarp();
       const int gsize = next_group < b1 ? (int)(group_last - next_group + 1) : 0;
-      int k = 0;
+      // the next group's size (its offsets g_nxt are in the lanes already)
+      const int nsize = gsize > 0 && group_last + 1 < b1
+                            ? (int)((group_last + 1 + kLanes < b1 ? group_last + 1 + kLanes : b1) -
+                                    (group_last + 1))
+                            : 0;
+      const int64_t group_last_off = __shfl_sync(kFull, g_off, gsize > 0 ? gsize - 1 : 0);
+      int k = 0, byte = 0;
       uint32_t bits = 0;
       for (;;) {
         // this lane's next error byte, if any
-        if (bits == 0 && nonzero != 0) {
+        while (bits == 0 && nonzero != 0) {
           k = __ffs(nonzero) - 1;
           nonzero &= nonzero - 1;
           bits = err_words[k * kLanes + lane];
         }
         int64_t p = INT64_MAX;
         if (bits != 0) {
-          const int byte = (__ffs(bits) - 1) >> 3;
+          byte = (__ffs(bits) - 1) >> 3;
           // row pairs: bytes `byte` and byte + 2 are positions 2m and 2m+1
           // of one row, and the first decides for both (the same string, or
           // 2m+1 starts one, and a string's first three bytes are the head
           // check's); in a quad word every byte is a row of its own
-          static_assert(!kBatchQuads, "the pair rule below");
-          bits &= ~(0x00FF00FFu << (8 * byte));
-          p = tile_lo + (int64_t)interleaved_position<ROWS, kBatchQuads>(k >> 3, k & 7, byte, lane);
+          if constexpr (kBatchQuads<ROWS>) bits &= ~(0xFFu << (8 * byte));
+          else bits &= ~(0x00FF00FFu << (8 * byte));
+          p = tile_lo + (int64_t)interleaved_position<ROWS, kBatchQuads<ROWS>>(k >> 3, k & 7, byte, lane);
         }
         uint32_t pending = __ballot_sync(kFull, p != INT64_MAX);
         if (pending == 0) break;
@@ -300,19 +337,36 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
           const int64_t q = __shfl_sync(kFull, p, src);
           const int cnt = __popc(__ballot_sync(kFull, g_off <= q));
           const int64_t lo_cnt = __shfl_sync(kFull, g_off, cnt > 0 ? cnt - 1 : 0);
+          // past the open group: the next group's offsets, before a search
+          const int cnt2 = __popc(__ballot_sync(kFull, g_nxt <= q));
+          const int64_t lo_cnt2 = __shfl_sync(kFull, g_nxt, cnt2 > 0 ? cnt2 - 1 : 0);
           if (lane == src) {
             int64_t own, o_lo, o_hi;
             if (cnt < gsize || gsize == 0) {
               own = next_group - 1 + cnt;
               o_lo = cnt > 0 ? lo_cnt : prev_off;
               o_hi = INT64_MAX;  // the next boundary lies past q
+            } else if (cnt2 < nsize) {
+              own = group_last + cnt2;
+              o_lo = cnt2 > 0 ? lo_cnt2 : group_last_off;
+              o_hi = INT64_MAX;
             } else {
               own = last_at_most(offsets, group_last, own_hi + 1, q);
               o_lo = own >= 0 && own <= count ? offsets[own] : 0;
               o_hi = own >= 0 && own < count ? offsets[own + 1] : 0;
             }
-            if (own >= 0 && own < count && q - o_lo >= 3 && q < o_hi)
-              charge<LOCATE>(out_valid, out_err, own, q - o_lo);
+            const bool charged = own >= 0 && own < count && q - o_lo >= 3 && q < o_hi;
+            if (charged) charge<LOCATE>(out_valid, out_err, own, q - o_lo);
+            if constexpr (kBatchQuads<ROWS>) {
+              // the next positions of the row are bytes `byte` of the next
+              // words: p + 1 is the same string or lies in the first three
+              // bytes of the next (the head check's), and so are p + 2 and
+              // p + 3 once p's string is charged
+              const int kk = k & 15;
+              const int last = charged ? 3 : 1;
+              for (int t = 1; t <= last && kk + t < 16; ++t)
+                err_words[(k + t) * kLanes + lane] &= ~(0xFFu << (8 * byte));
+            }
           }
         }
       }
@@ -362,14 +416,16 @@ __device__ __forceinline__ void batch_body(const uint8_t* __restrict__ data,
       open_group();
       take_windows(tile_lo, staged);
     }
-    // the 8 bytes before the next tile: this tile's last 8 (lane 31, last row)
-    __syncwarp();
+    // the 8 bytes before the next tile: this tile's last 8 (lane 31, last
+    // row), into the next slot's header
+    rd = rd + 1 == kStages ? 0 : rd + 1;
     if (lane == kLanes - 1) {
-      stage[2] = d[ROWS - 1].z;
-      stage[3] = d[ROWS - 1].w;
+      ring[rd * kSlotWords + 2] = d[ROWS - 1].z;
+      ring[rd * kSlotWords + 3] = d[ROWS - 1].w;
     }
     __syncwarp();
   }
+  cp_async_wait<0>();
 }
 
 template <int ROWS, bool LOCATE>
@@ -402,8 +458,8 @@ static cudaError_t launch_batch_rows(const uint8_t* data, const int64_t* offsets
                                      uint8_t* out_valid, int blocks_per_sm, int sm_count,
                                      cudaStream_t st, utf8_error_info* out_err = nullptr) {
   const unsigned grid = (unsigned)(sm_count * blocks_per_sm);
-  batch_kernel<ROWS, LOCATE><<<grid, kBlockThreads, 0, st>>>(data, offsets, count, out_valid,
-                                                              out_err);
+  batch_kernel<ROWS, LOCATE><<<grid, kBlockThreads, batch_smem_bytes<ROWS>(), st>>>(
+      data, offsets, count, out_valid, out_err);
   return cudaGetLastError();
 }
 
@@ -429,9 +485,9 @@ cudaError_t launch_batch_desc(const utf8_batch_desc* desc, const LaunchCfg& cfg,
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)(sm_count * cfg.batch_blocks_per_sm);
   switch (cfg.batch_rows) {
-    case 8: batch_desc_kernel<8><<<grid, kBlockThreads, 0, st>>>(desc); break;
-    case 4: batch_desc_kernel<4><<<grid, kBlockThreads, 0, st>>>(desc); break;
-    default: batch_desc_kernel<2><<<grid, kBlockThreads, 0, st>>>(desc); break;
+    case 8: batch_desc_kernel<8><<<grid, kBlockThreads, batch_smem_bytes<8>(), st>>>(desc); break;
+    case 4: batch_desc_kernel<4><<<grid, kBlockThreads, batch_smem_bytes<4>(), st>>>(desc); break;
+    default: batch_desc_kernel<2><<<grid, kBlockThreads, batch_smem_bytes<2>(), st>>>(desc); break;
   }
   return cudaGetLastError();
 }
@@ -481,16 +537,54 @@ cudaError_t launch_check_offsets(const int64_t* offsets, int64_t count, uint8_t*
 
 namespace utf8gpu {
 
+// Lets every batch kernel of `ROWS` rows use its rings' shared memory.
+template <int ROWS>
+static cudaError_t allow_batch_smem() {
+  const int smem = batch_smem_bytes<ROWS>();
+  cudaError_t e = cudaSuccess;
+  const auto allow = [&](const void* f) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
+  };
+  allow(reinterpret_cast<const void*>(batch_kernel<ROWS, false>));
+  allow(reinterpret_cast<const void*>(batch_kernel<ROWS, true>));
+  allow(reinterpret_cast<const void*>(batch_desc_kernel<ROWS>));
+  return e;
+}
+
+// Resident CTAs per SM of the batch kernels at `rows` rows, with their rings
+// (0 when this device cannot give them the shared memory).
 int batch_blocks_per_sm(int rows) {
   int n = 0;
   cudaError_t e;
   switch (rows) {
-    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<8, false>, kBlockThreads, 0); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<4, false>, kBlockThreads, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<2, false>, kBlockThreads, 0); break;
+    case 8:
+      e = allow_batch_smem<8>();
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<8, false>, kBlockThreads,
+                                                          batch_smem_bytes<8>());
+      break;
+    case 4:
+      e = allow_batch_smem<4>();
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<4, false>, kBlockThreads,
+                                                          batch_smem_bytes<4>());
+      break;
+    default:
+      e = allow_batch_smem<2>();
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<2, false>, kBlockThreads,
+                                                          batch_smem_bytes<2>());
+      break;
   }
-  if (e != cudaSuccess) { cudaGetLastError(); return 1; }
-  return n > 0 ? n : 1;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 }  // namespace utf8gpu

@@ -122,7 +122,12 @@ void clamp_to_occupancy(LaunchCfg& cfg) {
   if (cfg.rows != 2 && cfg.rows != 4 && cfg.rows != 8) cfg.rows = 8;
   if (cfg.batch_rows != 2 && cfg.batch_rows != 4 && cfg.batch_rows != 8) cfg.batch_rows = 8;
   const int v = validate_blocks_per_sm(cfg.rows);
-  const int b = batch_blocks_per_sm(cfg.batch_rows);
+  int b = batch_blocks_per_sm(cfg.batch_rows);
+  if (b < 1 && cfg.batch_rows != 2) {  // no room for the larger rings
+    cfg.batch_rows = 2;
+    b = batch_blocks_per_sm(2);
+  }
+  if (b < 1) b = 1;
   if (cfg.blocks_per_sm < 1 || cfg.blocks_per_sm > v) cfg.blocks_per_sm = v;
   if (cfg.batch_blocks_per_sm < 1 || cfg.batch_blocks_per_sm > b) cfg.batch_blocks_per_sm = b;
   apply_staged(cfg);
