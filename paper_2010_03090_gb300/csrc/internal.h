@@ -19,8 +19,8 @@ struct LaunchCfg {
   int blocks_per_sm = 8;  // resident CTAs per SM in the persistent grid
   int batch_rows = 8;     // tile rows for the batch kernel: 2, 4 or 8
   int batch_blocks_per_sm = 8;
-  // 8-row single- and multi-buffer passes stage their tiles through shared
-  // memory (tiles.cuh, warp_check_tiles_staged); set by clamp_to_occupancy
+  // 8-row single-buffer, multi-buffer and error-location passes stage their
+  // tiles through shared memory (tiles.cuh, StagedRun); set by clamp_to_occupancy
   // once this device's kernels accept the shared memory, never read from a
   // tuning cache
   bool staged = false;
@@ -30,6 +30,7 @@ struct LaunchCfg {
 // (validate.cu, buffers.cu); clamp_to_occupancy calls it.
 cudaError_t prepare_staged_kernels();
 cudaError_t prepare_buffers_staged();
+cudaError_t prepare_locate_staged();
 // Resident CTAs per SM of the staged single-buffer kernel (0 if it cannot run).
 int staged_blocks_per_sm();
 

@@ -17,10 +17,12 @@
 
 namespace utf8gpu {
 
-// Two CTAs per SM: with row quads the kernel fits 128 registers with a few
-// bytes spilled (160 without the bound, one CTA per SM and 2.4% slower than
-// row pairs; with the bound 3% faster than row pairs).
-template <int ROWS>
+// Two CTAs per SM: with row quads and register loads the kernel fits 128
+// registers with a few bytes spilled (160 without the bound, one CTA per SM
+// and 2.4% slower than row pairs; with the bound 3% faster than row pairs).
+// STAGED: the tiles come through the warp's ring in the launch's dynamic
+// shared memory (StagedRun, tiles.cuh), two tiles ahead.
+template <int ROWS, bool STAGED = false>
 __global__ void __launch_bounds__(kBlockThreads, 2)
     locate_kernel(Span s, uint64_t tiles, utf8_error_info* out) {
   constexpr uint64_t tb = TileGeom<ROWS>::kBytes;
@@ -43,14 +45,22 @@ __global__ void __launch_bounds__(kBlockThreads, 2)
   static_assert(poll_tiles >= 1, "a poll falls after whole tiles");
   const bool poll = poll_tiles < run.cnt;
   uint64_t best = poll ? load_position(out) : ~uint64_t(0);
-  uint4 next[ROWS];
-  load_run_tile<ROWS>(s, run, t0, 0, lane, lane_ptr, next);
+  uint4 next[STAGED ? 1 : ROWS];
+  extern __shared__ uint4 locate_rings[];
+  StagedRun<ROWS> ring(s, t0, t1, locate_rings + (threadIdx.x / kLanes) * kStages * ROWS * kLanes,
+                       lane);
+  if constexpr (STAGED) ring.start();
+  else load_run_tile<ROWS>(s, run, t0, 0, lane, lane_ptr, next);
   uint32_t tiles_to_look = poll_tiles;
   for (uint32_t k = 0; k < run.cnt; ++k, lane_ptr += tb) {
     uint4 d[ROWS];
+    if constexpr (STAGED) {
+      ring.next(k, d);
+    } else {
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) d[r] = next[r];
-    if (k + 1 < run.cnt) load_run_tile<ROWS>(s, run, t0, k + 1, lane, lane_ptr + tb, next);
+      for (int r = 0; r < ROWS; ++r) d[r] = next[r];
+      if (k + 1 < run.cnt) load_run_tile<ROWS>(s, run, t0, k + 1, lane, lane_ptr + tb, next);
+    }
     uint32_t e[ROWS / 2][8];
     check_tile<ROWS>(d, carry, lane, merge_sel, e);
     uint32_t any = 0;
@@ -62,14 +72,19 @@ __global__ void __launch_bounds__(kBlockThreads, 2)
       const uint32_t first = __reduce_min_sync(kFull, lane_first_error<ROWS>(e, lane));
       // virtual positions before s.off are zeros after zeros: never erroneous
       if (lane == 0) mark_first_error(out, (t0 + k) * tb + first - s.off);
+      if constexpr (STAGED) ring.finish();
       return;
     }
     if (poll && --tiles_to_look == 0) {  // (t0 + k + 1) * tb > s.off here
       tiles_to_look = poll_tiles;
-      if (__any_sync(kFull, best < (t0 + k + 1) * tb - s.off)) return;
+      if (__any_sync(kFull, best < (t0 + k + 1) * tb - s.off)) {
+        if constexpr (STAGED) ring.finish();
+        return;
+      }
       best = load_position(out);
     }
   }
+  if constexpr (STAGED) ring.finish();
 }
 
 __global__ void settle_kernel(const uint8_t* data, uint64_t n, utf8_error_info* out) {
@@ -86,30 +101,43 @@ __global__ void settle_batch_kernel(const uint8_t* __restrict__ data,
   }
 }
 
-template <int ROWS>
+template <int ROWS, bool STAGED>
 static int locate_occupancy() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, locate_kernel<ROWS>, kBlockThreads, 0) !=
-      cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &n, locate_kernel<ROWS, STAGED>, kBlockThreads,
+          STAGED ? staged_smem_bytes<ROWS>(kBlockThreads) : 0) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
   return n > 0 ? n : 1;
 }
 
-template <int ROWS>
+template <int ROWS, bool STAGED = false>
 static cudaError_t launch_locate_rows(const Span& s, utf8_error_info* out, int blocks_per_sm,
                                       int sm_count, cudaStream_t st) {
   const uint64_t tiles = span_tiles<ROWS>(s);
-  const int fit = locate_occupancy<ROWS>();
+  const int fit = locate_occupancy<ROWS, STAGED>();
   const int bps = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : fit;
   const uint64_t warps_per_block = kBlockThreads / kLanes;
   uint64_t grid = (uint64_t)sm_count * (uint64_t)bps;
   const uint64_t need = (tiles + warps_per_block - 1) / warps_per_block;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  locate_kernel<ROWS><<<(unsigned)grid, kBlockThreads, 0, st>>>(s, tiles, out);
+  locate_kernel<ROWS, STAGED>
+      <<<(unsigned)grid, kBlockThreads, STAGED ? staged_smem_bytes<ROWS>(kBlockThreads) : 0, st>>>(
+          s, tiles, out);
   return cudaGetLastError();
+}
+
+cudaError_t prepare_locate_staged() {
+  const int smem = staged_smem_bytes<8>(kBlockThreads);
+  cudaError_t e = cudaFuncSetAttribute(locate_kernel<8, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(locate_kernel<8, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  return e;
 }
 
 cudaError_t launch_locate(const uint8_t* data, uint64_t n, utf8_error_info* out,
@@ -120,7 +148,10 @@ cudaError_t launch_locate(const uint8_t* data, uint64_t n, utf8_error_info* out,
     switch (cfg.rows) {
       case 2: e = launch_locate_rows<2>(s, out, cfg.blocks_per_sm, sm_count, st); break;
       case 4: e = launch_locate_rows<4>(s, out, cfg.blocks_per_sm, sm_count, st); break;
-      default: e = launch_locate_rows<8>(s, out, cfg.blocks_per_sm, sm_count, st); break;
+      default:
+        e = cfg.staged ? launch_locate_rows<8, true>(s, out, cfg.blocks_per_sm, sm_count, st)
+                       : launch_locate_rows<8>(s, out, cfg.blocks_per_sm, sm_count, st);
+        break;
     }
   }
   if (e != cudaSuccess) return e;

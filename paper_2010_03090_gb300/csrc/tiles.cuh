@@ -503,22 +503,32 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-template <int ROWS, bool QUADS = kQuadRows<ROWS>>
-__device__ __forceinline__ uint32_t warp_check_tiles_staged(const Span& s, uint64_t t_begin,
-                                                            uint64_t t_end, uint4* ring) {
-  constexpr uint64_t tb = TileGeom<ROWS>::kBytes;
-  constexpr int kSlot = ROWS * kLanes;  // granules per slot
-  const int lane = threadIdx.x & (kLanes - 1);
-  uint32_t err = 0;
-  const uint32_t merge_sel = carry_merge_selector<QUADS>(lane);
-  Carry carry = ascii_carry();  // zeros before the stream
-  if (t_begin < t_end && t_begin > 0) carry = halo_carry<QUADS>(load_word(s, t_begin * tb - 4));
-  const RunTiles run = run_tiles<ROWS>(s, t_begin, t_end);
-  const uint8_t* lane_ptr = s.abase + t_begin * tb + lane * 16;
+// One warp's run of tiles through its ring: start() issues the first
+// kStages - 1 tiles; next(k, d) issues tile k + kStages - 1, waits for tile k
+// (the lane's own copies) and loads the lane's granules of it into d;
+// finish() waits for every copy still in flight (before a warp leaves early
+// or ends).  Tiles are taken in order, k = 0, 1, ...
+template <int ROWS>
+struct StagedRun {
+  static constexpr int kSlot = ROWS * kLanes;  // granules per slot
+  const Span& s;
+  RunTiles run;
+  uint64_t t_begin;
+  const uint8_t* lane_ptr;  // abase + t_begin * tile bytes + lane * 16
+  uint4* ring;
+  int lane;
+  int rd = 0, wr = kStages - 1;
+
+  __device__ __forceinline__ StagedRun(const Span& s_, uint64_t t_begin_, uint64_t t_end,
+                                       uint4* ring_, int lane_)
+      : s(s_), run(run_tiles<ROWS>(s_, t_begin_, t_end)), t_begin(t_begin_),
+        lane_ptr(s_.abase + t_begin_ * TileGeom<ROWS>::kBytes + lane_ * 16), ring(ring_),
+        lane(lane_) {}
+
   // tile t_begin + k into a slot: cp.async when interior, checked loads else
-  const auto issue = [&](uint32_t k, uint4* slot) {
+  __device__ __forceinline__ void issue(uint32_t k, uint4* slot) const {
     if (k - run.i0 < run.i_len) {
-      const uint8_t* p = lane_ptr + (uint64_t)k * tb;
+      const uint8_t* p = lane_ptr + (uint64_t)k * TileGeom<ROWS>::kBytes;
 #pragma unroll
       for (int r = 0; r < ROWS; ++r) cp_async16(&slot[r * kLanes + lane], p + r * kLanes * 16);
     } else {
@@ -527,23 +537,41 @@ __device__ __forceinline__ uint32_t warp_check_tiles_staged(const Span& s, uint6
       for (int r = 0; r < ROWS; ++r)
         slot[r * kLanes + lane] = load_granule(s, g0 + r * kLanes + lane);
     }
-  };
-#pragma unroll
-  for (int j = 0; j < kStages - 1; ++j) {
-    if ((uint32_t)j < run.cnt) issue((uint32_t)j, ring + j * kSlot);
-    cp_async_commit();
   }
-  int rd = 0, wr = kStages - 1;
-  for (uint32_t k = 0; k < run.cnt; ++k) {
+  __device__ __forceinline__ void start() const {
+#pragma unroll
+    for (int j = 0; j < kStages - 1; ++j) {
+      if ((uint32_t)j < run.cnt) issue((uint32_t)j, ring + j * kSlot);
+      cp_async_commit();
+    }
+  }
+  __device__ __forceinline__ void next(uint32_t k, uint4 (&d)[ROWS]) {
     if (k + kStages - 1 < run.cnt) issue(k + kStages - 1, ring + wr * kSlot);
-    cp_async_commit();  // one group per iteration, empty or not
+    cp_async_commit();  // one group per tile, empty or not
     cp_async_wait<kStages - 1>();  // tile k's group is complete
     const uint4* slot = ring + rd * kSlot;
-    uint4 d[ROWS];
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) d[r] = slot[r * kLanes + lane];
     rd = rd + 1 == kStages ? 0 : rd + 1;
     wr = wr + 1 == kStages ? 0 : wr + 1;
+  }
+  __device__ __forceinline__ void finish() const { cp_async_wait<0>(); }
+};
+
+template <int ROWS, bool QUADS = kQuadRows<ROWS>>
+__device__ __forceinline__ uint32_t warp_check_tiles_staged(const Span& s, uint64_t t_begin,
+                                                            uint64_t t_end, uint4* ring) {
+  constexpr uint64_t tb = TileGeom<ROWS>::kBytes;
+  const int lane = threadIdx.x & (kLanes - 1);
+  uint32_t err = 0;
+  const uint32_t merge_sel = carry_merge_selector<QUADS>(lane);
+  Carry carry = ascii_carry();  // zeros before the stream
+  if (t_begin < t_end && t_begin > 0) carry = halo_carry<QUADS>(load_word(s, t_begin * tb - 4));
+  StagedRun<ROWS> st(s, t_begin, t_end, ring, lane);
+  st.start();
+  for (uint32_t k = 0; k < st.run.cnt; ++k) {
+    uint4 d[ROWS];
+    st.next(k, d);
     uint32_t e[ROWS / 2][8];
     check_tile<ROWS, QUADS>(d, carry, lane, merge_sel, e);
 #pragma unroll
@@ -551,7 +579,7 @@ __device__ __forceinline__ uint32_t warp_check_tiles_staged(const Span& s, uint6
 #pragma unroll
       for (int m = 0; m < 8; ++m) err |= e[p][m];
   }
-  cp_async_wait<0>();
+  st.finish();
   return err;
 }
 

@@ -206,6 +206,7 @@ cudaError_t prepare_staged_kernels() {
                              cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess) e = prepare_buffers_staged();
+  if (e == cudaSuccess) e = prepare_locate_staged();
   if (e != cudaSuccess) cudaGetLastError();
   return e;
 }

@@ -1,4 +1,5 @@
-"""The two load paths of the 8-row single- and multi-buffer passes.
+"""The two load paths of the 8-row single-buffer, multi-buffer and
+error-location passes.
 
 By default (where the device accepts the shared memory) the warps stage their
 coming tiles through shared memory with cp.async, two tiles ahead; with
@@ -48,6 +49,7 @@ def check(buf, off=0):
     want = bool(oracle.valid(buf))
     assert bool(u.utf8_validate(view)) == want
     assert u.utf8_validate_buffers_async([view]).cpu().tolist() == [int(want)]
+    assert u.utf8_locate_error(view) == tuple(oracle.locate(buf))
     return want
 
 
@@ -102,7 +104,8 @@ def test_register_path_in_a_child():
         "        b[int(rng.integers(0, n))] = cls[i % cls.size]\n"
         "    np.save('_staged_case_%d.npy' % i, b)\n"
         "    t = torch.from_numpy(b).cuda()\n"
-        "    out.append([int(u.utf8_validate(t)), u.utf8_validate_buffers_async([t]).item()])\n"
+        "    out.append([int(u.utf8_validate(t)), u.utf8_validate_buffers_async([t]).item(),\n"
+        "                list(u.utf8_locate_error(t))])\n"
         "print(json.dumps(out))\n")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     env = dict(os.environ, UTF8GPU_STAGED="0")
@@ -116,9 +119,11 @@ def test_register_path_in_a_child():
         lines = r.stdout.strip().split("\n")
         assert lines[0] == "0", lines[0]
         got = json.loads(lines[1])
-        for i, (a, b) in enumerate(got):
-            want = int(oracle.valid(np.load(os.path.join(work, "_staged_case_%d.npy" % i))))
+        for i, (a, b, loc) in enumerate(got):
+            buf = np.load(os.path.join(work, "_staged_case_%d.npy" % i))
+            want = int(oracle.valid(buf))
             assert a == b == want, (i, a, b, want)
+            assert tuple(loc) == tuple(oracle.locate(buf)), (i, loc)
     finally:
         for i in range(24):
             f = os.path.join(work, "_staged_case_%d.npy" % i)
