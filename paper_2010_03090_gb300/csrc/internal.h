@@ -19,8 +19,9 @@ struct LaunchCfg {
   int blocks_per_sm = 8;  // resident CTAs per SM in the persistent grid
   int batch_rows = 8;     // tile rows for the batch kernel: 2, 4 or 8
   int batch_blocks_per_sm = 8;
-  // 8-row single-buffer, multi-buffer and error-location passes stage their
-  // tiles through shared memory (tiles.cuh, StagedRun); set by clamp_to_occupancy
+  // 8-row single-buffer, multi-buffer, error-location and stream-chunk passes
+  // stage their tiles through shared memory (tiles.cuh, StagedRun); set by
+  // clamp_to_occupancy
   // once this device's kernels accept the shared memory, never read from a
   // tuning cache
   bool staged = false;
@@ -31,6 +32,7 @@ struct LaunchCfg {
 cudaError_t prepare_staged_kernels();
 cudaError_t prepare_buffers_staged();
 cudaError_t prepare_locate_staged();
+cudaError_t prepare_chunk_staged();
 // Resident CTAs per SM of the staged single-buffer kernel (0 if it cannot run).
 int staged_blocks_per_sm();
 
@@ -87,10 +89,11 @@ cudaError_t launch_segments(const SegmentDesc* segs, const int64_t* tile_prefix,
 // One chunk of a longer stream (stream.cu): prefix = the up to three bytes
 // before it (natural order in bytes 1..3, b[-1] in byte 3) or, if prefix_dev
 // is set, read from device memory (b[-3], b[-2], b[-1]); tail_out, if set,
-// receives the stream's new last three bytes.
+// receives the stream's new last three bytes.  staged: 8-row tiles go through
+// shared memory (LaunchCfg::staged of the device).
 cudaError_t launch_chunk(const uint8_t* data, uint64_t n, uint32_t prefix,
                          const uint8_t* prefix_dev, int final_chunk, uint8_t* out_valid,
-                         uint8_t* tail_out, int sm_count, cudaStream_t st);
+                         uint8_t* tail_out, int sm_count, bool staged, cudaStream_t st);
 
 // Copies src to dst while validating it (copy.cu); result byte set by the call.
 cudaError_t launch_copy_validate(uint8_t* dst, const uint8_t* src, uint64_t n, uint8_t* out_valid,

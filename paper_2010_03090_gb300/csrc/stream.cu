@@ -40,7 +40,7 @@ __device__ __forceinline__ uint32_t chunk_prefix(const ChunkArgs& a) {
 
 // Clears the bytes of the interleaved error words whose virtual position
 // (relative to the stream's aligned base) is outside [lo, hi).
-template <int ROWS>
+template <int ROWS, bool QUADS>
 __device__ __forceinline__ void mask_positions(uint32_t (&e)[ROWS / 2][8], uint64_t tile_v,
                                                int lane, uint64_t lo, uint64_t hi) {
 #pragma unroll
@@ -49,7 +49,7 @@ __device__ __forceinline__ void mask_positions(uint32_t (&e)[ROWS / 2][8], uint6
     for (int m = 0; m < 8; ++m)
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        const uint64_t v = tile_v + interleaved_position<ROWS, false>(p, m, b, lane);
+        const uint64_t v = tile_v + interleaved_position<ROWS, QUADS>(p, m, b, lane);
         if (v < lo || v >= hi) e[p][m] &= ~(0xFFu << (8 * b));
       }
 }
@@ -57,8 +57,13 @@ __device__ __forceinline__ void mask_positions(uint32_t (&e)[ROWS / 2][8], uint6
 constexpr int kChunkRows = 8;       // tile rows per warp (4 KiB tiles), as the single-buffer default
 constexpr int kSmallChunkRows = 2;  // 1 KiB tiles for chunks too small to fill the grid
 
-template <int ROWS>
-__global__ void __launch_bounds__(kBlockThreads) chunk_kernel(Span s, uint64_t tiles, ChunkArgs a) {
+// STAGED (8 rows, where the device gives the rings their shared memory):
+// row quads with the tiles through the warp's ring (StagedRun, tiles.cuh);
+// otherwise row pairs with register loads (quads with register loads need
+// 145 registers, one CTA per SM).
+template <int ROWS, bool STAGED = false>
+__global__ void __launch_bounds__(kBlockThreads, 2) chunk_kernel(Span s, uint64_t tiles, ChunkArgs a) {
+  constexpr bool kQuads = STAGED;
   constexpr uint64_t tb = TileGeom<ROWS>::kBytes;
   const int lane = threadIdx.x & (kLanes - 1);
   const uint64_t warps = (uint64_t)gridDim.x * (kBlockThreads / kLanes);
@@ -75,26 +80,34 @@ __global__ void __launch_bounds__(kBlockThreads) chunk_kernel(Span s, uint64_t t
   const uint64_t t0 = tiles * w / warps;
   const uint64_t t1 = tiles * (w + 1) / warps;
   if (t0 >= t1) return;
-  const uint32_t merge_sel = carry_merge_selector<false>(lane);
+  const uint32_t merge_sel = carry_merge_selector<kQuads>(lane);
   Carry carry;
   if (t0 == 0) {
     // virtual bytes -4..-1 are data offsets -4-off .. -1-off
-    carry = halo_carry<false>(s.off < 4 ? pre << (8 * s.off) : 0u);
+    carry = halo_carry<kQuads>(s.off < 4 ? pre << (8 * s.off) : 0u);
   } else {
-    carry = halo_carry<false>(load_word(s, t0 * tb - 4));
+    carry = halo_carry<kQuads>(load_word(s, t0 * tb - 4));
   }
   const uint64_t keep_hi = a.final_chunk ? ~uint64_t(0) : s.off + s.n;
   uint64_t in0, in1;
   interior_tiles<ROWS>(s, in0, in1);
   const uint8_t* lane_ptr = s.abase + t0 * tb + lane * 16;
   uint32_t err = 0;
-  uint4 next[ROWS];  // the next tile's loads, issued one tile ahead
-  load_tile<ROWS>(s, t0, in0, in1, lane, lane_ptr, next);
+  uint4 next[STAGED ? 1 : ROWS];  // register form: the next tile's loads, one tile ahead
+  extern __shared__ uint4 chunk_rings[];
+  StagedRun<ROWS> ring(s, t0, t1, chunk_rings + (threadIdx.x / kLanes) * kStages * ROWS * kLanes,
+                       lane);
+  if constexpr (STAGED) ring.start();
+  else load_tile<ROWS>(s, t0, in0, in1, lane, lane_ptr, next);
   for (uint64_t t = t0; t < t1; ++t, lane_ptr += tb) {
     uint4 d[ROWS];
+    if constexpr (STAGED) {
+      ring.next((uint32_t)(t - t0), d);
+    } else {
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) d[r] = next[r];
-    if (t + 1 < t1) load_tile<ROWS>(s, t + 1, in0, in1, lane, lane_ptr + tb, next);
+      for (int r = 0; r < ROWS; ++r) d[r] = next[r];
+      if (t + 1 < t1) load_tile<ROWS>(s, t + 1, in0, in1, lane, lane_ptr + tb, next);
+    }
     if (t == 0 && lane == 0) {
       // prefix byte i (data offset i - 4) sits at virtual position off + i - 4
 #pragma unroll
@@ -109,26 +122,28 @@ __global__ void __launch_bounds__(kBlockThreads) chunk_kernel(Span s, uint64_t t
       }
     }
     uint32_t e[ROWS / 2][8];
-    check_tile<ROWS, false>(d, carry, lane, merge_sel, e);
+    check_tile<ROWS, kQuads>(d, carry, lane, merge_sel, e);
     const uint64_t tile_v = t * tb;
-    if (tile_v < s.off || tile_v + tb > keep_hi) mask_positions<ROWS>(e, tile_v, lane, s.off, keep_hi);
+    if (tile_v < s.off || tile_v + tb > keep_hi)
+      mask_positions<ROWS, kQuads>(e, tile_v, lane, s.off, keep_hi);
 #pragma unroll
     for (int p = 0; p < ROWS / 2; ++p)
 #pragma unroll
       for (int m = 0; m < 8; ++m) err |= e[p][m];
   }
+  if constexpr (STAGED) ring.finish();
   if (__any_sync(kFull, err != 0) && lane == 0) *a.out_valid = 0;
 }
 
-// Resident CTAs per SM of chunk_kernel (the same on every GPU of this
-// architecture; computed once, thread-safely).
-// Resident CTAs per SM of chunk_kernel<ROWS>.
-template <int ROWS>
+// Resident CTAs per SM of chunk_kernel<ROWS, STAGED> (the same on every GPU
+// of this architecture; computed once, thread-safely).
+template <int ROWS, bool STAGED>
 static int chunk_blocks_per_sm() {
   static const int n = [] {
     int k = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, chunk_kernel<ROWS>, kBlockThreads, 0) !=
-        cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &k, chunk_kernel<ROWS, STAGED>, kBlockThreads,
+            STAGED ? staged_smem_bytes<ROWS>(kBlockThreads) : 0) != cudaSuccess) {
       cudaGetLastError();
       k = 1;
     }
@@ -137,31 +152,45 @@ static int chunk_blocks_per_sm() {
   return n;
 }
 
-template <int ROWS>
+template <int ROWS, bool STAGED = false>
 static cudaError_t launch_chunk_rows(const Span& s, const ChunkArgs& a, int sm_count,
                                      cudaStream_t st) {
   const uint64_t tiles = span_tiles<ROWS>(s);
   const uint64_t warps_per_block = kBlockThreads / kLanes;
-  uint64_t grid = (uint64_t)sm_count * (uint64_t)chunk_blocks_per_sm<ROWS>();
+  uint64_t grid = (uint64_t)sm_count * (uint64_t)chunk_blocks_per_sm<ROWS, STAGED>();
   const uint64_t need = (tiles + warps_per_block - 1) / warps_per_block;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  chunk_kernel<ROWS><<<(unsigned)grid, kBlockThreads, 0, st>>>(s, tiles, a);
+  chunk_kernel<ROWS, STAGED>
+      <<<(unsigned)grid, kBlockThreads, STAGED ? staged_smem_bytes<ROWS>(kBlockThreads) : 0, st>>>(
+          s, tiles, a);
   return cudaGetLastError();
+}
+
+cudaError_t prepare_chunk_staged() {
+  const int smem = staged_smem_bytes<kChunkRows>(kBlockThreads);
+  cudaError_t e = cudaFuncSetAttribute(chunk_kernel<kChunkRows, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(chunk_kernel<kChunkRows, true>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  return e;
 }
 
 cudaError_t launch_chunk(const uint8_t* data, uint64_t n, uint32_t prefix,
                          const uint8_t* prefix_dev, int final_chunk, uint8_t* out_valid,
-                         uint8_t* tail_out, int sm_count, cudaStream_t st) {
+                         uint8_t* tail_out, int sm_count, bool staged, cudaStream_t st) {
   const Span s = make_span(data, n);
   const ChunkArgs a{prefix, prefix_dev, final_chunk, out_valid, tail_out};
   // A chunk so small that its 1 KiB tiles number at most the warps of the
   // persistent grid is checked in 1 KiB tiles: 4 KiB tiles would leave SMs
   // idle.
-  const uint64_t grid_warps = (uint64_t)sm_count * (uint64_t)chunk_blocks_per_sm<kChunkRows>() *
+  const uint64_t grid_warps = (uint64_t)sm_count * (uint64_t)chunk_blocks_per_sm<kChunkRows, false>() *
                               (kBlockThreads / kLanes);
   if (span_tiles<kSmallChunkRows>(s) <= grid_warps)
     return launch_chunk_rows<kSmallChunkRows>(s, a, sm_count, st);
+  if (staged) return launch_chunk_rows<kChunkRows, true>(s, a, sm_count, st);
   return launch_chunk_rows<kChunkRows>(s, a, sm_count, st);
 }
 
@@ -192,6 +221,7 @@ struct utf8_stream {
   uint8_t* dev = nullptr;  // [0..3]: tail slot 0, [4..7]: tail slot 1, [8]: result
   uint64_t chunks = 0;     // non-empty chunks since the last reset
   int sm_count = 0;
+  bool staged = false;     // the device's launch configuration stages 8-row tiles
 };
 
 extern "C" {
@@ -209,12 +239,13 @@ int utf8_validate_chunk(const uint8_t* data, size_t len, uint32_t prefix, int pr
   for (int k = 0; k < prefix_len; ++k) pre |= ((prefix >> (8 * k)) & 0xFFu) << (8 * (3 - k));
   if (len == 0 && !final_chunk) return set_thread_status(UTF8_OK);
   return status_of(launch_chunk(len ? data : out_valid, len, pre, nullptr, final_chunk, out_valid,
-                                nullptr, sms, stream));
+                                nullptr, sms, current_config().staged, stream));
 }
 
 utf8_stream* utf8_stream_create(void) {
   utf8_stream* s = new utf8_stream();
   s->sm_count = current_sm_count();
+  s->staged = current_config().staged;
   cudaError_t e = s->sm_count > 0 ? cudaMalloc(&s->dev, 16) : cudaErrorNoDevice;
   if (e == cudaSuccess) e = cudaMemset(s->dev, 0, 16);
   if (e == cudaSuccess) e = cudaMemset(s->dev + 8, 1, 1);
@@ -244,7 +275,7 @@ int utf8_stream_update(utf8_stream* s, const uint8_t* chunk, size_t len, cudaStr
   const uint8_t* tail_in = s->dev + 4 * (s->chunks & 1);
   uint8_t* tail_out = s->dev + 4 * ((s->chunks + 1) & 1);
   const cudaError_t e =
-      launch_chunk(chunk, len, 0, tail_in, 0, s->dev + 8, tail_out, s->sm_count, stream);
+      launch_chunk(chunk, len, 0, tail_in, 0, s->dev + 8, tail_out, s->sm_count, s->staged, stream);
   if (e == cudaSuccess) s->chunks += 1;
   return status_of(e);
 }
@@ -255,7 +286,7 @@ int utf8_stream_finish(utf8_stream* s, uint8_t* out_valid, cudaStream_t stream) 
   // end of stream: an empty final chunk after the current tail
   const uint8_t* tail_in = s->dev + 4 * (s->chunks & 1);
   cudaError_t e = launch_chunk(s->dev + 12, 0, 0, tail_in, 1, s->dev + 8, nullptr, s->sm_count,
-                               stream);
+                               s->staged, stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out_valid, s->dev + 8, 1, cudaMemcpyDeviceToDevice, stream);
   return status_of(e);

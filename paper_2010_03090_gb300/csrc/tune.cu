@@ -115,6 +115,7 @@ LaunchCfg tuned_config(const char* gpu_name, int sm_count) {
 static void apply_staged(LaunchCfg& cfg) {
   cfg.staged = cfg.rows == 8 && env_int("UTF8GPU_STAGED", 1) != 0 &&
                prepare_staged_kernels() == cudaSuccess &&
+               prepare_chunk_staged() == cudaSuccess &&
                cfg.blocks_per_sm <= staged_blocks_per_sm();
 }
 

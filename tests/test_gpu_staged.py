@@ -1,5 +1,5 @@
-"""The two load paths of the 8-row single-buffer, multi-buffer and
-error-location passes.
+"""The two load paths of the 8-row single-buffer, multi-buffer,
+error-location and stream-chunk passes.
 
 By default (where the device accepts the shared memory) the warps stage their
 coming tiles through shared memory with cp.async, two tiles ahead; with
@@ -41,6 +41,20 @@ def grid_warps():
     return c["sm_count"] * c["blocks_per_sm"] * 8
 
 
+def streamed(view, cuts):
+    """The stream's flag, the buffer given in chunks cut at `cuts`."""
+    h = u.utf8_stream_create()
+    try:
+        edges = [0] + sorted(cuts) + [view.numel()]
+        for a, b in zip(edges[:-1], edges[1:]):
+            u.utf8_stream_update(h, view[a:b])
+        out = torch.zeros(1, dtype=torch.uint8, device="cuda")
+        u.utf8_stream_finish(h, out)
+        return int(out.item())
+    finally:
+        u.utf8_stream_destroy(h)
+
+
 def check(buf, off=0):
     pool = torch.zeros(buf.size + 32, dtype=torch.uint8, device="cuda")
     if buf.size:
@@ -50,6 +64,8 @@ def check(buf, off=0):
     assert bool(u.utf8_validate(view)) == want
     assert u.utf8_validate_buffers_async([view]).cpu().tolist() == [int(want)]
     assert u.utf8_locate_error(view) == tuple(oracle.locate(buf))
+    # chunks of several tiles each (4 KiB tiles), cut inside characters too
+    assert streamed(view, [buf.size // 3 + 1, 2 * buf.size // 3 + 2]) == int(want)
     return want
 
 
@@ -104,8 +120,14 @@ def test_register_path_in_a_child():
         "        b[int(rng.integers(0, n))] = cls[i % cls.size]\n"
         "    np.save('_staged_case_%d.npy' % i, b)\n"
         "    t = torch.from_numpy(b).cuda()\n"
+        "    h = u.utf8_stream_create()\n"
+        "    for a, b in ((0, n // 3 + 1), (n // 3 + 1, 2 * n // 3 + 2), (2 * n // 3 + 2, n)):\n"
+        "        u.utf8_stream_update(h, t[min(a, n):min(b, n)])\n"
+        "    f = torch.zeros(1, dtype=torch.uint8, device='cuda')\n"
+        "    u.utf8_stream_finish(h, f)\n"
+        "    u.utf8_stream_destroy(h)\n"
         "    out.append([int(u.utf8_validate(t)), u.utf8_validate_buffers_async([t]).item(),\n"
-        "                list(u.utf8_locate_error(t))])\n"
+        "                list(u.utf8_locate_error(t)), int(f.item())])\n"
         "print(json.dumps(out))\n")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     env = dict(os.environ, UTF8GPU_STAGED="0")
@@ -119,10 +141,10 @@ def test_register_path_in_a_child():
         lines = r.stdout.strip().split("\n")
         assert lines[0] == "0", lines[0]
         got = json.loads(lines[1])
-        for i, (a, b, loc) in enumerate(got):
+        for i, (a, b, loc, st) in enumerate(got):
             buf = np.load(os.path.join(work, "_staged_case_%d.npy" % i))
             want = int(oracle.valid(buf))
-            assert a == b == want, (i, a, b, want)
+            assert a == b == st == want, (i, a, b, st, want)
             assert tuple(loc) == tuple(oracle.locate(buf)), (i, loc)
     finally:
         for i in range(24):
