@@ -583,4 +583,44 @@ __device__ __forceinline__ uint32_t warp_check_tiles_staged(const Span& s, uint6
   return err;
 }
 
+// warp_check_tiles_polling through the ring: every kPollBytes the warp votes
+// on the errors it has found and looks at the result byte it loaded
+// kPollBytes earlier, and leaves (after its copies in flight) once either
+// shows an error.
+template <int ROWS, bool QUADS = kQuadRows<ROWS>>
+__device__ __forceinline__ uint32_t warp_check_tiles_staged_polling(const Span& s, uint64_t t_begin,
+                                                                    uint64_t t_end, uint4* ring,
+                                                                    const uint8_t* result) {
+  constexpr uint64_t tb = TileGeom<ROWS>::kBytes;
+  constexpr uint32_t poll_tiles = kPollBytes / (uint32_t)tb;
+  static_assert(poll_tiles >= 1, "a poll falls after whole tiles");
+  const int lane = threadIdx.x & (kLanes - 1);
+  uint32_t err = 0;
+  const uint32_t merge_sel = carry_merge_selector<QUADS>(lane);
+  Carry carry = ascii_carry();  // zeros before the stream
+  if (t_begin < t_end && t_begin > 0) carry = halo_carry<QUADS>(load_word(s, t_begin * tb - 4));
+  StagedRun<ROWS> st(s, t_begin, t_end, ring, lane);
+  const bool poll = poll_tiles < st.run.cnt;
+  uint32_t seen = poll ? load_result(result) : 1u;
+  st.start();
+  uint32_t to_look = poll_tiles;
+  for (uint32_t k = 0; k < st.run.cnt; ++k) {
+    uint4 d[ROWS];
+    st.next(k, d);
+    uint32_t e[ROWS / 2][8];
+    check_tile<ROWS, QUADS>(d, carry, lane, merge_sel, e);
+#pragma unroll
+    for (int p = 0; p < ROWS / 2; ++p)
+#pragma unroll
+      for (int m = 0; m < 8; ++m) err |= e[p][m];
+    if (poll && --to_look == 0 && k + 1 < st.run.cnt) {
+      to_look = poll_tiles;
+      if (__any_sync(kFull, err != 0 || seen == 0)) break;
+      seen = load_result(result);
+    }
+  }
+  st.finish();
+  return err;
+}
+
 }  // namespace utf8gpu

@@ -24,7 +24,8 @@ namespace utf8gpu {
 // Two CTAs per SM: the register form of the row-quad classification fits 128
 // registers with a few bytes spilled (without the bound it takes 141, one CTA
 // per SM); the staged form (STAGED: tiles through shared memory, the
-// launch's dynamic shared memory holding each warp's ring) takes 115.
+// launch's dynamic shared memory holding each warp's ring) takes 124, with or
+// without early exit (POLL).
 template <int ROWS, bool POLL, bool STAGED = false>
 __global__ void __launch_bounds__(kBlockThreads, 2) validate_kernel(Span s, uint64_t t_first,
                                                                 uint64_t tiles,
@@ -35,10 +36,10 @@ __global__ void __launch_bounds__(kBlockThreads, 2) validate_kernel(Span s, uint
   const uint64_t t1 = t_first + tiles * (w + 1) / warps;
   uint32_t err;
   if constexpr (STAGED) {
-    static_assert(!POLL, "the staged form has no early exit");
     extern __shared__ uint4 validate_rings[];
-    err = warp_check_tiles_staged<ROWS>(
-        s, t0, t1, validate_rings + (threadIdx.x / kLanes) * kStages * ROWS * kLanes);
+    uint4* ring = validate_rings + (threadIdx.x / kLanes) * kStages * ROWS * kLanes;
+    if constexpr (POLL) err = warp_check_tiles_staged_polling<ROWS>(s, t0, t1, ring, out_valid);
+    else err = warp_check_tiles_staged<ROWS>(s, t0, t1, ring);
   } else if constexpr (POLL) {
     err = warp_check_tiles_polling<ROWS>(s, t0, t1, out_valid);
   } else {
@@ -82,17 +83,22 @@ static cudaError_t launch_rows(const Span& s, uint64_t t_begin, uint64_t t_end,
   const uint64_t need = (tiles + warps_per_block - 1) / warps_per_block;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  if (early_exit_enabled()) {
-    validate_kernel<ROWS, true><<<(unsigned)grid, kBlockThreads, 0, st>>>(s, t_begin, tiles, out_valid);
-    return cudaGetLastError();
-  }
+  const bool poll = early_exit_enabled();
   if constexpr (ROWS == 8) {
     if (cfg.staged) {
-      validate_kernel<ROWS, false, true>
-          <<<(unsigned)grid, kBlockThreads, staged_smem_bytes<ROWS>(kBlockThreads), st>>>(
-              s, t_begin, tiles, out_valid);
+      constexpr int smem = staged_smem_bytes<ROWS>(kBlockThreads);
+      if (poll)
+        validate_kernel<ROWS, true, true>
+            <<<(unsigned)grid, kBlockThreads, smem, st>>>(s, t_begin, tiles, out_valid);
+      else
+        validate_kernel<ROWS, false, true>
+            <<<(unsigned)grid, kBlockThreads, smem, st>>>(s, t_begin, tiles, out_valid);
       return cudaGetLastError();
     }
+  }
+  if (poll) {
+    validate_kernel<ROWS, true><<<(unsigned)grid, kBlockThreads, 0, st>>>(s, t_begin, tiles, out_valid);
+    return cudaGetLastError();
   }
   validate_kernel<ROWS, false><<<(unsigned)grid, kBlockThreads, 0, st>>>(s, t_begin, tiles, out_valid);
   return cudaGetLastError();
@@ -194,33 +200,39 @@ cudaError_t preload_validate_kernels() {
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, validate_kernel<8, false>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, validate_kernel<8, true>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, validate_kernel<8, false, true>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, validate_kernel<8, true, true>);
   return e;
 }
 
 cudaError_t prepare_staged_kernels() {
   const int smem = staged_smem_bytes<8>(kBlockThreads);
-  cudaError_t e = cudaFuncSetAttribute(validate_kernel<8, false, true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(validate_kernel<8, false, true>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
+  cudaError_t e = cudaSuccess;
+  for (const void* f : {reinterpret_cast<const void*>(validate_kernel<8, false, true>),
+                        reinterpret_cast<const void*>(validate_kernel<8, true, true>)}) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
+  }
   if (e == cudaSuccess) e = prepare_buffers_staged();
   if (e == cudaSuccess) e = prepare_locate_staged();
   if (e != cudaSuccess) cudaGetLastError();
   return e;
 }
 
+// (the smaller of the forms with and without early exit)
 int staged_blocks_per_sm() {
-  int n = 0;
+  const int smem = staged_smem_bytes<8>(kBlockThreads);
+  int n = 0, m = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, validate_kernel<8, false, true>,
-                                                    kBlockThreads,
-                                                    staged_smem_bytes<8>(kBlockThreads)) !=
-      cudaSuccess) {
+                                                    kBlockThreads, smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, validate_kernel<8, true, true>,
+                                                    kBlockThreads, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  return n;
+  return n < m ? n : m;
 }
 
 int validate_blocks_per_sm(int rows) {

@@ -106,7 +106,8 @@ def test_host_path_tile_ranges():
 
 def test_register_path_in_a_child():
     """UTF8GPU_STAGED=0 (read when a device is first used, so in a child):
-    the register form answers as the oracle does on the same cases."""
+    the register form answers as the oracle does on the same cases, with
+    early exit off and on."""
     code = (
         "import json, numpy as np, torch, paper_2010_03090_gb300 as u, synth\n"
         "print(json.loads(u.utf8_config_json())['staged'])\n"
@@ -126,8 +127,11 @@ def test_register_path_in_a_child():
         "    f = torch.zeros(1, dtype=torch.uint8, device='cuda')\n"
         "    u.utf8_stream_finish(h, f)\n"
         "    u.utf8_stream_destroy(h)\n"
+        "    u.utf8_set_early_exit(True)\n"
+        "    ee = int(u.utf8_validate(t))\n"
+        "    u.utf8_set_early_exit(False)\n"
         "    out.append([int(u.utf8_validate(t)), u.utf8_validate_buffers_async([t]).item(),\n"
-        "                list(u.utf8_locate_error(t)), int(f.item())])\n"
+        "                list(u.utf8_locate_error(t)), int(f.item()), ee])\n"
         "print(json.dumps(out))\n")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     env = dict(os.environ, UTF8GPU_STAGED="0")
@@ -141,10 +145,10 @@ def test_register_path_in_a_child():
         lines = r.stdout.strip().split("\n")
         assert lines[0] == "0", lines[0]
         got = json.loads(lines[1])
-        for i, (a, b, loc, st) in enumerate(got):
+        for i, (a, b, loc, st, ee) in enumerate(got):
             buf = np.load(os.path.join(work, "_staged_case_%d.npy" % i))
             want = int(oracle.valid(buf))
-            assert a == b == st == want, (i, a, b, st, want)
+            assert a == b == st == ee == want, (i, a, b, st, ee, want)
             assert tuple(loc) == tuple(oracle.locate(buf)), (i, loc)
     finally:
         for i in range(24):
