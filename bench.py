@@ -472,7 +472,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     # end to end, on every rank at once: host buffers through the public
     # host-memory entry point; all ranks' bytes over the slowest rank's time
     e2e_steps = 1 if "e2e" in legs else 0
-    e2e_value, e2e_flags = None, flags
+    e2e_value, e2e_flags, link_gbs = None, flags, None
     if e2e_steps:
         pinned = []
         for b in host:
@@ -488,7 +488,16 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             e2e_flags = [u.utf8_validate_host(p, stream=stream) for p in pinned]
         e2e_dt = max_over_ranks(time.perf_counter() - t, dist, "cuda")
         e2e_value = world * bytes_per_step * e2e_steps / e2e_dt / 1e9
-        del pinned
+        # the host link on this machine: plain copies of the same pinned buffers
+        # (no validation), to read the host path against
+        sink = torch.empty(max(p.numel() for p in pinned), dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for p in pinned:
+            sink[:p.numel()].copy_(p, non_blocking=True)
+        torch.cuda.synchronize()
+        link_gbs = bytes_per_step / (time.perf_counter() - t) / 1e9
+        del pinned, sink
 
     if rank != 0:
         if dist:
@@ -585,6 +594,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "e2e": {"value": round(e2e_value, 1) if e2e_value else None, "unit": "GB/s",
                 "h2d_bytes_per_step": bytes_per_step, "d2h_bytes_per_step": len(host),
                 "steps": e2e_steps, "api": "utf8_validate_host (pinned host buffers)",
+                "link_h2d_gbs": round(link_gbs, 1) if link_gbs else None,
+                "fraction_of_link": (round(e2e_value / world / link_gbs, 3)
+                                     if e2e_value and link_gbs else None),
                 "flags_ok": [bool(f) for f in e2e_flags] == [bool(f) for f in flags]},
         "gpu_launches": args.steps,
         "clocks": clock_info,
